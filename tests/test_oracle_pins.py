@@ -1,0 +1,324 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: numerical
+quadrature, brute-force velocity-space integration, exact polynomial data,
+closed-form solutions and the invariants the paper states (well balance,
+conservation, uniform-flow consistency, order of accuracy).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import oracle as orc
+from paper_2306_04467_gb300 import inputs
+
+G = 9.81
+
+
+# ---------------------------------------------------------------------------
+# half-space Maxwellian moments (Sec. 2.2; Eq. g-SWE) vs adaptive quadrature
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("U,lam", [(0.0, 0.1), (0.37, 0.05), (-1.2, 0.2), (2.5, 0.01), (-0.01, 1.3)])
+def test_half_moments_match_quadrature(U, lam):
+    dens = lambda u: math.sqrt(lam / math.pi) * math.exp(-lam * (u - U) ** 2)
+    for half, (a, b) in ((1, (0, np.inf)), (-1, (-np.inf, 0)), (0, (-np.inf, np.inf))):
+        mu = orc.raw_moments(U, lam, half, 7)
+        for k in range(8):
+            ref, _ = integrate.quad(lambda u: u ** k * dens(u), a, b, epsabs=1e-14, epsrel=1e-13, limit=200)
+            scale = max(1.0, abs(ref), (1.0 / lam) ** (k / 2))
+            assert abs(mu[k] - ref) <= 2e-12 * scale, (half, k, mu[k], ref)
+
+
+# ---------------------------------------------------------------------------
+# time integrals of the coefficients C1..C5 printed under Eq. SWE-2nd-order
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("tau,delta", [(0.05e-3, 1e-3), (2e-3, 1e-3), (1e-4, 5e-4), (0.3, 0.7)])
+def test_time_integrals_match_quadrature(tau, delta):
+    C = [lambda t: 1 - math.exp(-t / tau),
+         lambda t: -tau * (1 - math.exp(-t / tau)) + t * math.exp(-t / tau),
+         lambda t: -tau * (1 - math.exp(-t / tau)) + t,
+         lambda t: math.exp(-t / tau),
+         lambda t: -t * math.exp(-t / tau)]
+    q = orc.time_integrals(tau, delta)
+    for i in range(5):
+        ref, _ = integrate.quad(C[i], 0, delta, epsabs=0, epsrel=1e-13, limit=200)
+        scale = max(abs(ref), delta * min(delta, tau))
+        assert abs(q[i] - ref) <= 1e-11 * scale, (i, q[i], ref)
+
+
+# ---------------------------------------------------------------------------
+# the interface solution f (Eq. SWE-2nd-order) integrated by brute force
+# ---------------------------------------------------------------------------
+def _gl_composite(a, b, panels, order=8):
+    x, w = np.polynomial.legendre.leggauss(order)
+    edges = np.linspace(a, b, panels + 1)
+    xs = []
+    ws = []
+    for i in range(panels):
+        lo, hi = edges[i], edges[i + 1]
+        xs.append(0.5 * (hi - lo) * x + 0.5 * (hi + lo))
+        ws.append(0.5 * (hi - lo) * w)
+    return np.concatenate(xs), np.concatenate(ws)
+
+
+def _brute_force_parts(l, r, g):
+    """Velocity moments (psi and u psi weights) of the five parts of f, by
+    dense Gauss-Legendre quadrature over (u, v) with the split at u = 0."""
+    spread = 14.0 * math.sqrt(g * max(l[0], r[0]))
+    umax = max(abs(l[1]), abs(r[1])) + spread
+    vlo = min(l[2], r[2]) - spread
+    vhi = max(l[2], r[2]) + spread
+    un, uw_n = _gl_composite(-umax, 0.0, 80)
+    up, uw_p = _gl_composite(0.0, umax, 80)
+    v, vw = _gl_composite(vlo, vhi, 120)
+    u = np.concatenate([un, up])
+    uw = np.concatenate([uw_n, uw_p])
+    H = (u > 0).astype(float)[:, None]
+    uu, vv = np.meshgrid(u, v, indexing="ij")
+    Wq = uw[:, None] * vw[None, :]
+
+    def mx(h, U, V):
+        lam = 1.0 / (g * h)
+        return h * lam / math.pi * np.exp(-lam * ((uu - U) ** 2 + (vv - V) ** 2)), lam
+
+    def slope(h, U, V, lam, dn, dt):
+        c2 = (uu - U) ** 2 + (vv - V) ** 2
+        out = 0.0
+        for d, vel in ((dn, uu), (dt, vv)):
+            K = lam * d[0] / h * c2 + 2 * lam * ((uu - U) * (d[1] - U * d[0]) / h + (vv - V) * (d[2] - V * d[0]) / h)
+            out = out + K * vel
+        return out
+
+    def force(U, V, lam, pn, pt):
+        c2 = (uu - U) ** 2 + (vv - V) ** 2
+        return -lam * lam * c2 * (pn * (uu - U) + pt * (vv - V))
+
+    w6 = [np.ones_like(uu), uu, vv, uu, uu * uu, uu * vv]
+    mom = lambda F: np.array([np.sum(Wq * F * w) for w in w6])
+    gl_, laml = mx(l[0], l[1], l[2])
+    gr_, lamr = mx(r[0], r[1], r[2])
+    m4 = mom(gl_ * H + gr_ * (1 - H))
+    hb, mb, nb = m4[0], m4[1], m4[2]
+    Ub, Vb = mb / hb, nb / hb
+    gb, lamb = mx(hb, Ub, Vb)
+    kbl = slope(hb, Ub, Vb, lamb, l[3:6], l[6:9]) + force(Ub, Vb, lamb, l[9], l[10])
+    kbr = slope(hb, Ub, Vb, lamb, r[3:6], r[6:9]) + force(Ub, Vb, lamb, r[9], r[10])
+    p2 = gb * (kbl * H + kbr * (1 - H))
+    d = -mom(p2)[:3]
+    A = lamb * d[0] / hb * ((uu - Ub) ** 2 + (vv - Vb) ** 2) + \
+        2 * lamb * ((uu - Ub) * (d[1] - Ub * d[0]) / hb + (vv - Vb) * (d[2] - Vb * d[0]) / hb)
+    kl = slope(l[0], l[1], l[2], laml, l[3:6], l[6:9]) + force(l[1], l[2], laml, l[9], l[10])
+    kr = slope(r[0], r[1], r[2], lamr, r[3:6], r[6:9]) + force(r[1], r[2], lamr, r[9], r[10])
+    parts = [mom(gb), mom(p2), mom(gb * A), m4, mom(gl_ * kl * H + gr_ * kr * (1 - H))]
+    return np.array(parts)
+
+
+def _random_side(rng, h):
+    return np.array([h, rng.uniform(-1.5, 1.5), rng.uniform(-1, 1),
+                     *rng.uniform(-0.5, 0.5, 3), *rng.uniform(-0.5, 0.5, 3),
+                     rng.uniform(-3, 3), rng.uniform(-3, 3)])
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_point_solution_matches_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    l = _random_side(rng, rng.uniform(0.3, 1.5))
+    r = _random_side(rng, rng.uniform(0.3, 1.5))
+    parts = _brute_force_parts(l, r, G)
+    for tau, delta in ((1e-4, 2e-3), (3e-3, 1e-3)):
+        q = np.array([integrate.quad(f, 0, delta, epsrel=1e-13)[0] for f in (
+            lambda t: 1 - math.exp(-t / tau),
+            lambda t: -tau * (1 - math.exp(-t / tau)) + t * math.exp(-t / tau),
+            lambda t: -tau * (1 - math.exp(-t / tau)) + t,
+            lambda t: math.exp(-t / tau),
+            lambda t: -t * math.exp(-t / tau))])
+        ref = q @ parts
+        W, F = orc.gks_point(l, r, G, tau, delta)
+        scale = np.abs(q) @ np.abs(parts)
+        assert np.all(np.abs(W - ref[:3]) <= 1e-11 * scale[:3] + 1e-16), (W, ref[:3])
+        assert np.all(np.abs(F - ref[3:]) <= 1e-11 * scale[3:] + 1e-16), (F, ref[3:])
+
+
+def test_uniform_state_gives_physical_flux():
+    """Equal states, no slopes, no force: the fitted interface flux is the
+    physical two-layer flux F(W) of Eq. SWE-macro and the value is W."""
+    for h, U, V in ((1.0, 0.3, -0.2), (0.2, -1.1, 0.4), (0.8, 0.0, 0.0)):
+        s = np.array([h, U, V, 0, 0, 0, 0, 0, 0, 0, 0])
+        tau, delta = 5e-5, 1e-3
+        W1, F1 = orc.gks_point(s, s, G, tau, delta)
+        W2, F2 = orc.gks_point(s, s, G, tau, delta / 2)
+        F = (4 * F2 - F1) / delta
+        Ft = 4 * (F1 - 2 * F2) / delta ** 2
+        W = (4 * W2 - W1) / delta
+        phys = np.array([h * U, h * U * U + 0.5 * G * h * h, h * U * V])
+        assert np.allclose(F, phys, rtol=1e-14, atol=1e-14)
+        assert np.allclose(W, [h, h * U, h * V], rtol=1e-14, atol=1e-14)
+        assert np.all(np.abs(Ft) <= 1e-9 * (1 + np.abs(phys)))
+
+
+# ---------------------------------------------------------------------------
+# S2O4 time stepping (Eq. SWE-fully-discrete) is fourth order on y' = a y
+# ---------------------------------------------------------------------------
+def test_s2o4_is_fourth_order():
+    a = -1.3 + 0.0j
+    errs = []
+    for n in (10, 20, 40):
+        dt = 1.0 / n
+        y = 1.0
+        for _ in range(n):
+            L, Lt = a.real * y, a.real ** 2 * y
+            ys = orc.s2o4(1, y, L, Lt, 0.0, dt)
+            y = orc.s2o4(2, y, L, Lt, a.real ** 2 * ys, dt)
+        errs.append(abs(y - math.exp(a.real)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(3.8 < o < 4.3 for o in orders), orders
+
+
+# ---------------------------------------------------------------------------
+# reconstruction (Eqs. Recons-eqs .. Recons-system) and the Gauss theorem
+# ---------------------------------------------------------------------------
+def _cubic(rng):
+    c = rng.normal(size=10)
+
+    def f(x, y):
+        return (c[0] + c[1] * x + c[2] * y + c[3] * x * x + c[4] * x * y + c[5] * y * y
+                + c[6] * x ** 3 + c[7] * x * x * y + c[8] * x * y * y + c[9] * y ** 3)
+
+    def fx(x, y):
+        return c[1] + 2 * c[3] * x + c[4] * y + 3 * c[6] * x * x + 2 * c[7] * x * y + c[8] * y * y
+
+    def fy(x, y):
+        return c[2] + c[4] * x + 2 * c[5] * y + c[7] * x * x + 2 * c[8] * x * y + 3 * c[9] * y * y
+    return f, fx, fy
+
+
+def _interior_cells(mesh, margin):
+    P = mesh.xy[mesh.tri]
+    cx = P[:, :, 0].mean(1)
+    cy = P[:, :, 1].mean(1)
+    x0, x1, y0, y1 = mesh.domain
+    return np.nonzero((cx > x0 + margin) & (cx < x1 - margin) & (cy > y0 + margin) & (cy < y1 - margin))[0]
+
+
+@pytest.mark.parametrize("degree", [1, 3])
+def test_reconstruction_reproduces_polynomials(degree):
+    """P3 least squares is exact for cubics (linear weights); every candidate,
+    hence the nonlinear combination, is exact for linear data."""
+    rng = np.random.default_rng(7 + degree)
+    mesh = inputs.jittered_mesh(10, 10, seed=11, bc="wall")
+    fs = []
+    for v in range(6):
+        f, fx, fy = _cubic(rng)
+        if degree == 1:
+            c0, c1, c2 = rng.normal(size=3)
+            f = (lambda a, b, c: (lambda x, y: a + b * x + c * y))(c0, c1, c2)
+            fx = (lambda b: (lambda x, y: b + 0 * x))(c1)
+            fy = (lambda c: (lambda x, y: c + 0 * x))(c2)
+        if v in (0, 3):
+            f = (lambda g: (lambda x, y: 3.0 + g(x, y)))(f)   # positive depths
+        fs.append((f, fx, fy))
+    avg = np.stack([inputs.cell_average(f, mesh, 5) for f, _, _ in fs])
+    grad = np.stack([np.stack([inputs.cell_average(fx, mesh, 5), inputs.cell_average(fy, mesh, 5)]) for _, fx, fy in fs])
+    o = orc.Oracle(mesh, None, gamma_hi=1.0 if degree == 3 else orc.GAMMA_HI)
+    o.set_state(avg, grad)
+    o.reconstruct()
+    cells = _interior_cells(mesh, 0.25)
+    assert len(cells) >= 40
+    worst = 0.0
+    for c in cells:
+        P = mesh.xy[mesh.tri[c]]
+        for bary in ((0.2, 0.3), (0.6, 0.1), (0.05, 0.9)):
+            x, y = P[0] + bary[0] * (P[1] - P[0]) + bary[1] * (P[2] - P[0])
+            val, g = o.eval(c, x, y)
+            for v, (f, fx, fy) in enumerate(fs):
+                worst = max(worst, abs(val[v] - f(x, y)), abs(g[v, 0] - fx(x, y)), abs(g[v, 1] - fy(x, y)))
+    assert worst < 1e-9, worst
+
+
+def test_weno_weights_tend_to_linear_on_smooth_data():
+    errs = []
+    for n in (8, 16, 32):
+        p = inputs.smooth_periodic(n)
+        o = orc.Oracle.from_problem(p)
+        o.reconstruct()
+        om = o.omega()
+        errs.append(np.abs(om[:, [0, 3]] / orc.GAMMA_HI - 1).max())
+    # the deviation from the linear weights vanishes under refinement
+    assert errs[1] < errs[0] / 8 and errs[2] < errs[1] / 8 and errs[2] < 1e-3, errs
+
+
+def test_gauss_theorem_gradient_exact_for_cubics():
+    """Eq. slope-1 with 2-point Gauss per edge is exact for cubic data."""
+    rng = np.random.default_rng(5)
+    mesh = inputs.jittered_mesh(9, 7, domain=(0, 1.3, 0, 1), seed=3, bc="wall")
+    o = orc.Oracle(mesh)
+    f, fx, fy = _cubic(rng)
+    xq, _ = o.edge_points()
+    pv = f(xq[..., 0], xq[..., 1])
+    g = o.gauss_gradient(pv)
+    ref = np.stack([inputs.cell_average(fx, mesh, 5), inputs.cell_average(fy, mesh, 5)], 1)
+    assert np.abs(g - ref).max() < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# whole-scheme invariants named by the paper
+# ---------------------------------------------------------------------------
+def test_uniform_flow_stays_uniform():
+    p = inputs.smooth_periodic(8)
+    avg = np.zeros_like(p.avg)
+    avg[:, :] = np.array([1.0, 0.3, -0.2, 0.7, 0.1, 0.05])[:, None]
+    o = orc.Oracle(p.mesh, None, g=G, chi=0.98)
+    o.set_state(avg, np.zeros_like(p.grad))
+    o.advance(6)
+    a, g = o.get_state()
+    assert np.abs(a - avg).max() < 1e-13
+    assert np.abs(g).max() < 1e-11
+
+
+def test_lake_at_rest_is_preserved():
+    """h1 + B = const, h2 = const, U = 0 over a non-flat bottom (Sec. 3.2, Sec. 4.2)."""
+    p = inputs.lake_at_rest(24)
+    o = orc.Oracle.from_problem(p)
+    o.advance(40)
+    a, g = o.get_state()
+    bav = p.b_vert[p.mesh.tri].mean(1)
+    assert np.abs(a[3] + bav - 0.8).max() <= 1e-12
+    assert np.abs(a[0] - 0.2).max() <= 1e-12
+    assert np.abs(a[[1, 2, 4, 5]]).max() <= 1e-12
+
+
+@pytest.mark.parametrize("case", ["periodic", "walls"])
+def test_mass_is_conserved(case):
+    if case == "periodic":
+        p = inputs.smooth_periodic(12)
+    else:
+        p = inputs.interface_dambreak(10)
+    o = orc.Oracle.from_problem(p)
+    m0 = o.mass()
+    o.advance(20)
+    m1 = o.mass()
+    assert np.all(np.abs(m1 - m0) <= 1e-13 * np.abs(m0)), (m1 - m0) / m0
+
+
+def _l1(prob, o):
+    a, _ = o.get_state()
+    ex, _ = prob.exact(o.t)
+    area, _, _ = o.geometry()
+    return np.sum(area * np.abs(a[3] - ex[3])) / np.sum(area)
+
+
+def test_convergence_order_on_smooth_translation():
+    """Exact translation (periodic analogue of Sec. 4.1): the L1 error of h1
+    falls at least at second order under refinement (the paper attributes the
+    loss from fourth order to the second-order interlayer source)."""
+    errs = []
+    for n in (8, 16, 32):
+        p = inputs.translation(n, t_end=0.02)
+        o = orc.Oracle.from_problem(p)
+        o.advance(10 ** 6, t_end=p.t_end)
+        assert abs(o.t - p.t_end) < 1e-12
+        errs.append(_l1(p, o))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert orders[-1] >= 2.0, (errs, orders)
