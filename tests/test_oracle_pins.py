@@ -322,3 +322,46 @@ def test_convergence_order_on_smooth_translation():
         errs.append(_l1(p, o))
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
     assert orders[-1] >= 2.0, (errs, orders)
+
+
+def test_linear_internal_wave_speed_and_mode():
+    """Linearising Eq. SWE-macro about rest on a flat bottom gives
+    d2/dt2 (h1, h2) = G [[H1, chi H1], [H2, H2]] d2/dx2 (h1, h2): the slow
+    (internal) eigenpair fixes both the speed and the layer ratio of a wave.
+    A small right-going internal wave must travel at that speed without
+    exciting the fast external mode (which places chi on the lower layer)."""
+    H1, H2, chi, amp = 0.6, 0.4, 0.8, 1e-4
+    lam, vec = np.linalg.eig(G * np.array([[H1, chi * H1], [H2, H2]]))
+    lam, vec = lam.real, vec.real   # real spectrum: the system is hyperbolic here
+    k = int(np.argmin(lam))
+    c = math.sqrt(lam[k])
+    r = vec[:, k] / vec[0, k]
+    mesh = inputs.jittered_mesh(32, 4, domain=(0, 1, 0, 0.125), seed=9, bc="periodic")
+    tp = 2 * math.pi
+
+    def state(t):
+        f = lambda x, y: np.sin(tp * (x - c * t))
+        fx = lambda x, y: tp * np.cos(tp * (x - c * t))
+        avg = np.zeros((6, mesh.n_tri))
+        grad = np.zeros((6, 2, mesh.n_tri))
+        F = inputs.cell_average(f, mesh, 5)
+        Fx = inputs.cell_average(fx, mesh, 5)
+        for base, H, rr in ((3, H1, r[0]), (0, H2, r[1])):
+            avg[base] = H + amp * rr * F
+            grad[base, 0] = amp * rr * Fx
+            # u = c h'/H, so h u = c h' (1 + h'/H): keep the linear part
+            avg[base + 1] = c * amp * rr * F
+            grad[base + 1, 0] = c * amp * rr * Fx
+        return avg, grad
+
+    a0, g0 = state(0.0)
+    o = orc.Oracle(mesh, None, g=G, chi=chi)
+    o.set_state(a0, g0)
+    T = 0.25 / c
+    o.advance(10 ** 6, t_end=T)
+    a, _ = o.get_state()
+    ex, _ = state(o.t)
+    area, _, _ = o.geometry()
+    for base in (3, 0):
+        err = np.sum(area * np.abs(a[base] - ex[base])) / np.sum(area * np.abs(ex[base] - ex[base].mean()))
+        assert err < 0.02, (base, err)
