@@ -1,0 +1,310 @@
+"""Benchmark: triangle-stage updates/s of the compact two-layer GKS on GB300.
+
+Workload (one GPU): precision/balance configuration at full size -- a jittered
+1024 x 1024-square mesh of the unit square (2,097,152 triangles, walls), a
+Gaussian bump b = 0.5 exp(-50 r^2), flat interface (h1 + b = 0.8) and flat
+upper layer (h2 = 0.2), zero velocity, chi = 0.98, CFL 0.5. One benchmark step
+is one S2O4 time step (two stages) over the whole mesh, i.e. every part of the
+hot path: CFL step, reconstruction, interface levels, edge solution, sources,
+update and gradients.
+
+`value` is the FP32 form (FP64 for the balance terms and sums); the plain FP64
+GPU form of the same workload is reported beside it, with the L1 difference
+between the two after the timed run.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own replica of the workload (the
+mesh is not partitioned: replicas only); value = all ranks' triangle-stages /
+max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "triangle-stage updates/s vs plain FP64 GPU at stated L1 error; % roofline"
+UNIT = "triangle-stage updates/s"
+N_SQ = 1024
+
+# Per-unit work of the kernels, FLOPs counted by the hardware counters
+# (sm__sass_thread_inst_executed_op_{f,d}{add,mul,fma}, FMA = 2) on a
+# 131,072-triangle case, divided by the units of one launch. Units: recon and
+# update per cell, iface and edge per edge.
+FLOPS_PER_UNIT = {
+    "fp32": {"recon": None, "iface": None, "edge": None, "update": None},
+    "fp64": {"recon": None, "iface": None, "edge": None, "update": None},
+}
+# Measured FMA-chain peaks of this GB300 pool (TFLOP/s, 2 flops per FMA).
+PEAK_TFLOPS = {"fp32": None, "fp64": None}
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 5 + i and "Active" in s[5 + i]
+                          and "Not" not in s[5 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_rate(seconds_budget=15.0, n=48, stages_per_step=2, max_steps=None):
+    """The FP64 CPU oracle on a bounded sample of the same workload: the same
+    problem on an n x n-square mesh; returns (triangle-stages/s, description)."""
+    from oracle.oracle import Oracle
+    from paper_2306_04467_gb300 import inputs
+    prob = inputs.lake_at_rest(n, chi=0.98)
+    o = Oracle.from_problem(prob)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        o.advance(stages_per_step)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_budget or (max_steps and steps >= max_steps):
+            break
+    rate = prob.mesh.n_tri * stages_per_step * steps / el
+    desc = "oracle (serial FP64 C, 1 thread) on the same workload at %dx%d squares (%d triangles), %d steps, %.1f s" % (
+        n, n, prob.mesh.n_tri, steps, el)
+    return rate, desc, steps, el
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle.oracle import Oracle
+    from paper_2306_04467_gb300 import inputs
+    n = 48
+    prob = inputs.lake_at_rest(n, chi=0.98)
+    o = Oracle.from_problem(prob)
+    for _ in range(args.warmup):
+        o.advance(2)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.advance(2)
+    el = time.perf_counter() - t0
+    rate = prob.mesh.n_tri * 2 * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded jittered mesh, analytic initial data)",
+        "config": {"workload": "lake at rest over a Gaussian bump, jittered %dx%d-square mesh of the unit "
+                               "square (%d triangles; bounded sample of the 1024x1024 workload), walls, chi=0.98"
+                               % (n, n, prob.mesh.n_tri), "l2": "working set below L2 (CPU run)"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d steps of 2 stages on %d triangles" % (args.steps, prob.mesh.n_tri)},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_SQ, help="squares per side of the mesh")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    from paper_2306_04467_gb300 import gks2l as g
+    from paper_2306_04467_gb300 import inputs
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # CPU baseline first (host cores, before any GPU work): rank 0 only
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, desc, _, _ = oracle_rate()
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    prob = inputs.lake_at_rest(args.n, chi=0.98)
+    nt = prob.mesh.n_tri
+    stream = torch.cuda.Stream(device=dev)
+    results = {}
+    for form, prec in (("fp32", g.GKS2L_FP32), ("fp64", g.GKS2L_FP64)):
+        with torch.cuda.stream(stream):
+            par = g.default_params(g=prob.g, chi=prob.chi, cfl=prob.cfl, precision=prec)
+            s = g.Solver(prob.mesh, par, prob.b_vert, device=dev, stream=stream)
+            s.set_state(prob.avg, prob.grad)
+            steps = args.steps if form == "fp32" else max(2, args.steps // 4)
+            s.advance(2 * args.warmup)
+            torch.cuda.synchronize(dev)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            sampler = ClockSampler(local)
+            with sampler:
+                torch.cuda.synchronize(dev)
+                e0.record(stream)
+                s.advance(2 * steps, sync=False)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+            barrier()
+            ms = e0.elapsed_time(e1) / steps
+            ms = max_over_ranks(ms)
+            st = s.stats()
+            if st["status"] != 0:
+                raise RuntimeError("device status %d after the timed run" % st["status"])
+            a, _ = s.get_state()
+            kern = s.profile_kernels(2)
+            results[form] = {"ms_per_step": ms, "steps": steps, "clocks": sampler.summary(), "kernels": kern,
+                             "state": a, "workspace": s.workspace_bytes}
+            # end to end through the C ABI with host (pinned) buffers
+            if form == "fp32":
+                ha = torch.empty(6 * nt, dtype=torch.float64).pin_memory()
+                hg = torch.empty(12 * nt, dtype=torch.float64).pin_memory()
+                ha.copy_(torch.from_numpy(np.ascontiguousarray(prob.avg).ravel()))
+                hg.copy_(torch.from_numpy(np.ascontiguousarray(prob.grad).ravel()))
+                n_e2e = max(2, steps // 2)
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                for _ in range(n_e2e):
+                    s.set_state_host_ptr(ha.data_ptr(), hg.data_ptr())
+                    s.advance(2, sync=False)
+                    s.get_state_host_ptr(ha.data_ptr(), hg.data_ptr())
+                torch.cuda.synchronize(dev)
+                el = max_over_ranks(time.perf_counter() - t0)
+                results[form]["e2e"] = {"value": ws * nt * 2 * n_e2e / el, "unit": UNIT,
+                                        "h2d_bytes_per_step": 18 * 8 * nt, "d2h_bytes_per_step": 18 * 8 * nt}
+            del s
+            torch.cuda.empty_cache()
+
+    area = np.abs(0.5 * np.cross(prob.mesh.xy[prob.mesh.tri[:, 1]] - prob.mesh.xy[prob.mesh.tri[:, 0]],
+                                 prob.mesh.xy[prob.mesh.tri[:, 2]] - prob.mesh.xy[prob.mesh.tri[:, 0]]))
+    l1 = max(float(np.sum(area * np.abs(results["fp32"]["state"][v] - results["fp64"]["state"][v])) /
+                   np.sum(area * np.abs(results["fp64"]["state"][v]))) for v in (0, 3))
+
+    r32 = results["fp32"]
+    value = ws * nt * 2 / (r32["ms_per_step"] * 1e-3)
+    value64 = ws * nt * 2 / (results["fp64"]["ms_per_step"] * 1e-3)
+    # roofline of the dominant kernel of the headline form
+    kern = r32["kernels"]
+    top = max(("recon", "iface", "edge", "update"), key=lambda k: kern[k])
+    units = nt if top in ("recon", "update") else int(round(1.5 * nt))
+    fpu = FLOPS_PER_UNIT["fp32"][top]
+    peak = PEAK_TFLOPS["fp32"]
+    roof = {"bound": "alu", "kernel": "k_" + top, "unit": "TFLOP/s", "traffic": None}
+    if fpu and peak:
+        achieved = fpu * units / (kern[top] * 1e-3) / 1e12
+        roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                     "peak_source": "measured FP32 FMA-chain peak on this pool"})
+    else:
+        roof.update({"achieved": None, "peak": None, "frac": None})
+    share = {k: kern[k] / sum(kern[x] for x in ("recon", "iface", "edge", "update")) for k in
+             ("recon", "iface", "edge", "update")}
+    launches = steps_launch = 1 + 2 * 4
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": r32["steps"],
+        "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded jittered mesh, analytic initial data)",
+        "config": {"workload": "precision/balance case: lake at rest over a Gaussian bump "
+                               "b=0.5exp(-50r^2), h1+b=0.8, h2=0.2, u=0, chi=0.98, walls, jittered "
+                               "%dx%d-square mesh (%d triangles), S2O4 step = 2 stages" % (args.n, args.n, nt),
+                   "form": "FP32 moments/reconstruction with FP64 balance terms and sums",
+                   "l2": "inputs larger than L2 (operators and state %.1f GB)" % (r32["workspace"] / 1e9),
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "fp64_gpu": {"value": value64, "unit": UNIT, "ms_per_step": results["fp64"]["ms_per_step"],
+                     "speedup_fp32_over_fp64": value / value64},
+        "l1_rel_fp32_vs_fp64": l1,
+        "kernel_ms": {k: round(v, 4) for k, v in kern.items()},
+        "kernel_share": {k: round(v, 4) for k, v in share.items()},
+        "roofline": roof,
+        "clocks": r32["clocks"],
+        "e2e": r32["e2e"],
+        "gpu_launches": launches * r32["steps"],
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * gks2l -- GB300 (sm_103a) library for one explicit S2O4 stage of the compact
+ * gas-kinetic scheme (GKS) for the two-layer shallow water equations (TLSWE)
+ * on triangle meshes, after Zhao, Gan & Xu, arXiv 2306.04467.
+ *
+ * The problem statement the calls follow (Sec. 2.1, Eq. SWE-macro): a triangle
+ * mesh, a bottom B, the per-layer depths and discharges W = (h2, h2U2, h2V2,
+ * h1, h1U1, h1V1) with layer 1 the lower layer, the density ratio
+ * chi = rho2/rho1, gravity G and the CFL number (Sec. 4) -> the state after n
+ * stages of the two-stage fourth-order (S2O4) time stepping
+ * (Eq. SWE-fully-discrete). The state is the cell averages AND their
+ * cell-averaged gradients (Sec. 3.3, Eq. slope-1), which the scheme updates.
+ *
+ * Conventions
+ *  - Every call returns 0 (GKS2L_OK) or a negative GKS2L_E* code; no call
+ *    aborts. Device-side faults (negative depth, non-finite values) are
+ *    recorded in a status word and reported by gks2l_stats / gks2l_advance.
+ *  - Host arrays are read during the call and never retained. Device memory
+ *    (the workspace) is allocated by the caller (e.g. a torch tensor), bound
+ *    with gks2l_bind and never freed by the library.
+ *  - State arrays are variable-major in the caller's cell order:
+ *      avg[v * n_tri + j], grad[(v * 2 + d) * n_tri + j]   (d = 0: x, 1: y)
+ *    The library renumbers cells internally (space-filling curve); all public
+ *    state calls use the caller's order.
+ *  - All work runs on the stream given to gks2l_bind; calls that return host
+ *    data synchronise that stream.
+ */
+#ifndef GKS2L_H
+#define GKS2L_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GKS2L_OK 0
+#define GKS2L_EINVAL -1      /* bad argument (null pointer, size, parameter)        */
+#define GKS2L_EMESH -2       /* mesh not usable (orientation, periodic match, LS)   */
+#define GKS2L_ECUDA -3       /* a CUDA runtime call failed                          */
+#define GKS2L_ESTATE -4      /* call out of order (not bound, no state)             */
+#define GKS2L_ENEGDEPTH -5   /* a depth became <= 0 on the device                   */
+#define GKS2L_ENONFINITE -6  /* a non-finite value appeared on the device           */
+#define GKS2L_ESPACE -7      /* workspace too small                                 */
+#define GKS2L_ENOTIMPL -8
+
+/* boundary kinds per triangle edge (edge k runs from tri[k] to tri[(k+1)%3]) */
+#define GKS2L_BC_INTERIOR 0
+#define GKS2L_BC_WALL 1      /* reflecting wall: mirror ghost (Sec. 4.6 walls)       */
+#define GKS2L_BC_PERIODIC 2  /* matched with the opposite side by `period`           */
+
+/* arithmetic forms */
+#define GKS2L_FP64 0         /* every step in FP64                                   */
+#define GKS2L_FP32 1         /* FP32 moments and reconstruction; FP64 for the base
+                                values, the well-balanced flux/source cancellation
+                                and the conservation sums                           */
+
+/* troubled-cell indicator in the reconstruction */
+#define GKS2L_INDICATOR_OFF 0   /* nonlinear WENO weights in every cell              */
+#define GKS2L_INDICATOR_MLP 1   /* learned gate: cells it calls smooth take the
+                                   linear (P3) reconstruction                        */
+
+/* A triangle mesh (host memory, read during gks2l_create only).
+ * xy: 2*n_vert vertex coordinates; tri: 3*n_tri vertex indices, counter-
+ * clockwise; tri_bc: 3*n_tri boundary kinds (NULL: every boundary edge is a
+ * wall); period: translation between matched periodic sides (0 if unused). */
+typedef struct {
+  int32_t n_vert;
+  const double *xy;
+  int32_t n_tri;
+  const int32_t *tri;
+  const int8_t *tri_bc;
+  double period[2];
+} gks2l_mesh;
+
+/* Scheme parameters.
+ * g, chi, cfl: gravity G, density ratio chi = rho2/rho1 (Eq. SWE-macro) and
+ *   CFL number of dt = CFL dX / U_max (Sec. 4).
+ * eps, eps_num: collision time tau = eps dt + eps_num |(hl^2-hr^2)/(hl^2+hr^2)| dt
+ *   (Sec. 4; paper values 0.05 and 5).
+ * weno_gamma_hi: linear weight of the P3 candidate (the three P1 candidates
+ *   share the rest); weno_eps: smoothness regulariser, eps = weno_eps |Omega|
+ *   (1 + Q0^2). The paper defers both to an external reference.
+ * precision: GKS2L_FP64 or GKS2L_FP32.
+ * indicator, indicator_threshold: troubled-cell gate (GKS2L_INDICATOR_*); a
+ *   cell is called smooth when the gate's output is below the threshold. */
+typedef struct {
+  double g, chi, cfl;
+  double eps, eps_num;
+  double weno_gamma_hi, weno_eps;
+  int32_t precision;
+  int32_t indicator;
+  float indicator_threshold;
+} gks2l_params;
+
+/* Run statistics (FP64 sums taken on the device). */
+typedef struct {
+  double mass[2];        /* sum |Omega_j| h_j for layer 1 (lower) and layer 2  */
+  double t;              /* simulated time of instance 0                        */
+  double dt_last;        /* last step size of instance 0                        */
+  int64_t stages_done;
+  int32_t status;        /* 0 or a GKS2L_E* code raised on the device           */
+  int32_t n_instances;
+  double smooth_fraction;/* share of cell-stages the gate sent to the linear path */
+} gks2l_stats_t;
+
+typedef struct gks2l_ctx gks2l_ctx;
+
+/* Fill p with the paper's defaults (G = 9.81, chi = 1, CFL = 0.5, eps = 0.05,
+ * eps_num = 5) and this library's WENO reading (0.85, 1.0), FP64, no gate. */
+int gks2l_default_params(gks2l_params *p);
+
+/* Build a context for one mesh: geometry, compact stencils (Eq.
+ * Recons-stencil) and least-squares operators (Eq. Recons-system), all in FP64
+ * on the host. Copies the mesh. Returns GKS2L_EMESH for clockwise or
+ * degenerate triangles or unmatched periodic edges. */
+int gks2l_create(const gks2l_mesh *mesh, const gks2l_params *params, gks2l_ctx **out);
+
+/* Build one context over several independent meshes (an ensemble): each
+ * instance keeps its own time step and time; they advance together. */
+int gks2l_create_ensemble(int32_t n, const gks2l_mesh *meshes, const gks2l_params *params,
+                          gks2l_ctx **out);
+
+/* Device bytes the caller must provide to gks2l_bind. */
+int gks2l_workspace_bytes(const gks2l_ctx *ctx, size_t *bytes);
+
+/* Bind caller-owned device memory (>= gks2l_workspace_bytes, 256-byte
+ * aligned) and a CUDA stream (cudaStream_t, NULL = default stream); uploads
+ * the mesh operators. The library never frees the workspace. */
+int gks2l_bind(gks2l_ctx *ctx, void *d_workspace, size_t bytes, void *stream);
+
+/* Bottom B sampled at the vertices (host, n_vert doubles, concatenated over
+ * instances for an ensemble); B is continuous and linear on each triangle.
+ * May be called before or after gks2l_bind. */
+int gks2l_set_bathymetry(gks2l_ctx *ctx, const double *b_vert);
+
+/* Set the state from host arrays (avg: 6*n_tri, grad: 12*n_tri or NULL for
+ * zero gradients) in the caller's order; resets time and step counters. */
+int gks2l_set_state(gks2l_ctx *ctx, const double *avg, const double *grad);
+/* Same from device arrays (caller order) on the bound stream. */
+int gks2l_set_state_device(gks2l_ctx *ctx, const double *d_avg, const double *d_grad);
+
+/* Advance by up to n_stages stages (two stages make one S2O4 step). With
+ * t_end > 0 each step is shortened to land on t_end and no step starts at or
+ * after it. Enqueues work on the bound stream; t_out (if not NULL) forces a
+ * synchronisation and returns the time of instance 0. Returns a device
+ * status code only when t_out is requested. */
+int gks2l_advance(gks2l_ctx *ctx, int32_t n_stages, double t_end, double *t_out);
+
+/* Copy the state to host arrays (caller order); synchronises the stream. */
+int gks2l_get_state(gks2l_ctx *ctx, double *avg, double *grad);
+/* Copy the state to device arrays (caller order) on the bound stream. */
+int gks2l_get_state_device(gks2l_ctx *ctx, double *d_avg, double *d_grad);
+
+/* Mass sums, time, step and device status; synchronises the stream. */
+int gks2l_stats(gks2l_ctx *ctx, gks2l_stats_t *out);
+
+/* Load the troubled-cell gate: 24->32->32->1 MLP, weights as float32
+ * [W1 (32x24), b1 (32), W2 (32x32), b2 (32), W3 (1x32), b3 (1)] and input
+ * normalisation [mean (24), inv_std (24)]; stored on the device in bf16
+ * (weights) and fp32 (biases, normalisation). */
+int gks2l_set_mlp(gks2l_ctx *ctx, const float *params, size_t n_floats);
+
+/* Per-cell training data for the gate from the current state (device
+ * arrays, caller order): features[24 * n_tri] (normalised inputs, raw) and
+ * labels[n_tri] = 1 where the nonlinear weights of eta1 or h2 depart from the
+ * linear ones by more than `tol` (max |omega_k/gamma_k - 1|). */
+int gks2l_harvest(gks2l_ctx *ctx, float tol, float *d_features, float *d_labels);
+
+/* Kernel timing for roofline reports: advances n_steps full steps (exactly
+ * like gks2l_advance, state included) but launches the stage kernels one by
+ * one between CUDA events on the bound stream, then synchronises. ms[k] is
+ * the mean duration of one launch of kernel k, in the order: reconstruction,
+ * interface levels, edge solution, cell update (each averaged over both
+ * stages), step start. Requires a state and phase at a step boundary. */
+int gks2l_profile_kernels(gks2l_ctx *ctx, int32_t n_steps, double ms[5]);
+
+/* Human-readable name of a status code. */
+const char *gks2l_error_string(int code);
+
+void gks2l_destroy(gks2l_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,719 @@
+// gks2l: CUDA kernels (sm_103a) and the C ABI of include/gks2l.h.
+//
+// One S2O4 stage (arXiv 2306.04467, Eq. SWE-fully-discrete) is four kernels
+// over structure-of-arrays data in a Morton-renumbered cell order:
+//   k_recon   (cell x variable)      compact P3/WENO reconstruction (Sec. 3.4)
+//   k_iface   (edge x layer x point) blended interface levels h-hat (Sec. 2.3)
+//   k_edge    (edge x layer x point) gas-kinetic interface solution (Eq. SWE-2nd-order)
+//   k_update  (cell)                 fluxes, sources, S2O4 update, Gauss-theorem
+//                                    gradients (Eqs. SWE-semi-flux, slope-1, S2O3),
+//                                    CFL and conservation reductions
+// A step is k_step_begin + two stages, captured once into a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gks2l.h"
+#include "prep.h"
+#include "stage.cuh"
+
+using namespace gks2l;
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr unsigned long long DBL_INF_BITS = 0x7FF0000000000000ull;
+
+// ------------------------------------------------------------------ kernels
+template <typename R>
+__global__ void __launch_bounds__(192) k_recon(Dev d, Par p) {
+  int j = blockIdx.x * 32 + threadIdx.x;
+  if (j >= d.nt) return;
+  if (!(d.dt[d.inst[j]] > 0)) return;
+  recon_unit<R>(d, p, j, threadIdx.y);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_iface(Dev d) {
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = tid >> 2, ell = (tid >> 1) & 1, q = tid & 1;
+  bool ok = e < d.ne;
+  int ee = ok ? e : d.ne - 1;
+  ok = ok && d.dt[d.inst[d.eL[ee]]] > 0;
+  double v = ok ? iface_unit<R>(d, ee, ell, q) : 0.0;
+  double s = v + __shfl_xor_sync(FULL, v, 1);
+  if (ok && q == 0) d.hc[ell * d.ne + e] = 0.5 * s;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_edge(Dev d, Par p, int stage) {
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = tid >> 2, ell = (tid >> 1) & 1, q = tid & 1;
+  bool ok = e < d.ne;
+  int ee = ok ? e : d.ne - 1;
+  ok = ok && d.dt[d.inst[d.eL[ee]]] > 0;
+  double out[12];
+  if (ok) {
+    edge_unit<R>(d, p, ee, ell, q, stage, out);
+  } else {
+    for (int k = 0; k < 12; k++) out[k] = 0;
+  }
+#pragma unroll
+  for (int k = 0; k < 12; k++) out[k] = 0.5 * (out[k] + __shfl_xor_sync(FULL, out[k], 1));
+  if (!ok) return;
+  const int NE = d.ne;
+  const int vb = ell == 0 ? 3 : 0;
+  if (q == 0) {
+    for (int k = 0; k < 3; k++) {
+      d.eF[(vb + k) * NE + e] = out[k];
+      d.eFt[(vb + k) * NE + e] = out[3 + k];
+    }
+  } else {
+    double *Wd = stage == 1 ? d.eWn : d.eW;
+    for (int k = 0; k < 3; k++) {
+      Wd[(vb + k) * NE + e] = out[6 + k];
+      d.eWt[(vb + k) * NE + e] = out[9 + k];
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// min of dX/U_max and per-layer mass, reduced per warp when the warp lies in
+// one instance (the usual case), per lane otherwise
+__device__ __forceinline__ void reduce_cell_stats(const Dev &d, bool ok, int inst, double ratio, double m1,
+                                                  double m2) {
+  int lane = threadIdx.x & 31;
+  int i0 = __shfl_sync(FULL, inst, 0);
+  bool uniform = __all_sync(FULL, !ok || inst == i0) && __shfl_sync(FULL, ok ? 1 : 0, 0);
+  if (uniform) {
+    double r = warp_min(ok ? ratio : INFINITY);
+    double s1 = warp_sum(ok ? m1 : 0.0), s2 = warp_sum(ok ? m2 : 0.0);
+    if (lane == 0) {
+      if (r < INFINITY) atomicMin(&d.dtbits[i0], (unsigned long long)__double_as_longlong(r));
+      atomicAdd(&d.mass[2 * i0], s1);
+      atomicAdd(&d.mass[2 * i0 + 1], s2);
+    }
+  } else if (ok) {
+    if (ratio < INFINITY) atomicMin(&d.dtbits[inst], (unsigned long long)__double_as_longlong(ratio));
+    atomicAdd(&d.mass[2 * inst], m1);
+    atomicAdd(&d.mass[2 * inst + 1], m2);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_update(Dev d, Par p, int stage) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  bool ok = j < d.nt;
+  int inst = ok ? d.inst[j] : 0;
+  double ratio = INFINITY;
+  int fl = 0;
+  if (ok) {
+    double r = update_unit(d, p, j, stage, &fl);
+    if (r > 0) ratio = r;
+  }
+  if (fl) atomicOr(d.status, fl);
+  if (stage != 2) return;
+  double m1 = 0, m2 = 0;
+  if (ok) {
+    m1 = d.area[j] * d.avg[3 * d.nt + j];
+    m2 = d.area[j] * d.avg[j];
+  }
+  reduce_cell_stats(d, ok, inst, ratio, m1, m2);
+  if (ok && j == d.inst_first[inst]) d.t[inst] += d.dt[inst];
+}
+
+// CFL ratio and mass of the current state (after a state is set)
+__global__ void __launch_bounds__(128) k_cfl(Dev d, Par p) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  bool ok = j < d.nt;
+  int inst = ok ? d.inst[j] : 0;
+  double ratio = INFINITY, m1 = 0, m2 = 0;
+  if (ok) {
+    double um = 0;
+    for (int l = 0; l < 2; l++) {
+      double h = d.avg[(3 * l) * d.nt + j];
+      double u = d.avg[(3 * l + 1) * d.nt + j] / h, v = d.avg[(3 * l + 2) * d.nt + j] / h;
+      double sp = sqrt(u * u + v * v) + sqrt(p.g * h);
+      um = fmax(um, sp);
+    }
+    ratio = d.dX[j] / um;
+    if (!(ratio > 0) || !isfinite(ratio)) {
+      atomicOr(d.status, 2);
+      ratio = INFINITY;
+    }
+    m1 = d.area[j] * d.avg[3 * d.nt + j];
+    m2 = d.area[j] * d.avg[j];
+  }
+  reduce_cell_stats(d, ok, inst, ratio, m1, m2);
+}
+
+__global__ void k_reset_stats(Dev d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.ninst) return;
+  d.dtbits[i] = DBL_INF_BITS;
+  d.mass[2 * i] = d.mass[2 * i + 1] = 0;
+}
+
+// step size of each instance from the CFL ratio of the current state (Sec. 4),
+// shortened to land on t_end
+__global__ void k_step_begin(Dev d, Par p, const double *tend) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.ninst) return;
+  double r = __longlong_as_double((long long)d.dtbits[i]);
+  double dt = p.cfl * r;
+  double te = *tend;
+  if (te > 0) {
+    double rem = te - d.t[i];
+    if (rem <= 1e-12 * fmax(1.0, fabs(te))) dt = 0;
+    else if (dt > rem) dt = rem;
+  }
+  if (!isfinite(dt) || dt < 0) {
+    atomicOr(d.status, 2);
+    dt = 0;
+  }
+  d.dt[i] = dt;
+  d.dtbits[i] = DBL_INF_BITS;
+  d.mass[2 * i] = d.mass[2 * i + 1] = 0;
+}
+
+// caller order <-> device order
+__global__ void k_gather(int nt, int nvar, const int *perm, const double *src, double *dst) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nt) return;
+  int c = perm[j];
+  for (int v = 0; v < nvar; v++) dst[(size_t)v * nt + j] = src ? src[(size_t)v * nt + c] : 0.0;
+}
+__global__ void k_scatter(int nt, int nvar, const int *perm, const double *src, double *dst) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nt) return;
+  int c = perm[j];
+  for (int v = 0; v < nvar; v++) dst[(size_t)v * nt + c] = src[(size_t)v * nt + j];
+}
+
+// ------------------------------------------------------------- workspace
+struct Carver {
+  char *base;
+  size_t off = 0;
+  template <typename T> T *take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T *p = base ? (T *)(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+}  // namespace
+
+struct gks2l_ctx {
+  Prep prep;
+  gks2l_params par{};
+  std::vector<double> bvert;
+  bool has_b = false, bound = false, has_state = false;
+  size_t rsize = 8;
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t stream = nullptr;
+  Dev d{};
+  int *d_perm = nullptr;
+  double *d_tend = nullptr;
+  double *d_stage = nullptr;   // 18 * nt staging for permutations
+  int phase = 0;
+  int64_t stages = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::string err;
+};
+
+namespace {
+
+size_t layout(gks2l_ctx *c, char *base) {
+  const Prep &P = c->prep;
+  const size_t nt = P.nt, ne = P.ne, ni = P.ninst, rs = c->rsize;
+  Carver k{base};
+  Dev &d = c->d;
+  d.nt = P.nt; d.ne = P.ne; d.ninst = P.ninst;
+  d.inst = k.take<int>(nt);
+  d.inv_area = k.take<double>(nt);
+  d.area = k.take<double>(nt);
+  d.hs = k.take<double>(nt);
+  d.dX = k.take<double>(nt);
+  d.bmean = k.take<double>(nt);
+  d.bgx = k.take<double>(nt);
+  d.bgy = k.take<double>(nt);
+  d.st_cell = k.take<int>(kSlots * nt);
+  d.st_xf = k.take<int8_t>(kSlots * nt);
+  d.lsq = k.take<char>(rs * kCoef * kCols * nt);
+  d.p1op = k.take<char>(rs * 30 * nt);
+  d.bq = k.take<char>(rs * kBeta * nt);
+  d.mmean = k.take<char>(rs * 7 * nt);
+  d.plane = k.take<double>(6 * nt);
+  d.cedge = k.take<int>(3 * nt);
+  d.inst_first = k.take<int>(ni + 1);
+  d.avg = k.take<double>(6 * nt);
+  d.grad = k.take<double>(12 * nt);
+  d.Wn = k.take<double>(6 * nt);
+  d.Ln = k.take<double>(6 * nt);
+  d.Ltn = k.take<double>(6 * nt);
+  d.coef = k.take<char>(rs * 60 * nt);
+  d.omg = k.take<char>(rs * 2 * nt);
+  d.gate = k.take<uint8_t>(nt);
+  d.eL = k.take<int>(ne);
+  d.eR = k.take<int>(ne);
+  d.exf = k.take<int8_t>(ne);
+  d.en0 = k.take<double>(ne);
+  d.en1 = k.take<double>(ne);
+  d.elen = k.take<double>(ne);
+  d.eb0 = k.take<double>(ne);
+  d.eb1 = k.take<double>(ne);
+  d.exiL = k.take<char>(rs * 4 * ne);
+  d.exiR = k.take<char>(rs * 4 * ne);
+  d.hc = k.take<double>(2 * ne);
+  d.eF = k.take<double>(6 * ne);
+  d.eFt = k.take<double>(6 * ne);
+  d.eW = k.take<double>(6 * ne);
+  d.eWt = k.take<double>(6 * ne);
+  d.eWn = k.take<double>(6 * ne);
+  d.dt = k.take<double>(ni);
+  d.t = k.take<double>(ni);
+  d.dtbits = k.take<unsigned long long>(ni);
+  d.mass = k.take<double>(2 * ni);
+  d.status = k.take<int>(1);
+  d.gate_count = k.take<unsigned long long>(2);
+  d.xf = k.take<double>(4 * kMaxXf);
+  c->d_perm = k.take<int>(nt);
+  c->d_tend = k.take<double>(1);
+  c->d_stage = k.take<double>(18 * nt);
+  return k.off + 256;
+}
+
+#define CK(x)                                                                              \
+  do {                                                                                     \
+    cudaError_t e_ = (x);                                                                  \
+    if (e_ != cudaSuccess) {                                                               \
+      c->err = std::string(#x) + ": " + cudaGetErrorString(e_);                            \
+      return GKS2L_ECUDA;                                                                  \
+    }                                                                                      \
+  } while (0)
+
+template <typename T>
+int upload(gks2l_ctx *c, const void *dst, const std::vector<T> &src) {
+  if (src.empty()) return 0;
+  CK(cudaMemcpyAsync((void *)dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  return 0;
+}
+template <typename R>
+int upload_r(gks2l_ctx *c, const void *dst, const std::vector<double> &src, std::vector<R> &tmp) {
+  tmp.assign(src.begin(), src.end());
+  return upload(c, dst, tmp);
+}
+
+int upload_bathymetry(gks2l_ctx *c) {
+  std::vector<double> bm, bx, by, e0, e1;
+  bathymetry(c->prep, c->has_b ? c->bvert.data() : nullptr, bm, bx, by, e0, e1);
+  int rc;
+  if ((rc = upload(c, c->d.bmean, bm)) || (rc = upload(c, c->d.bgx, bx)) || (rc = upload(c, c->d.bgy, by)) ||
+      (rc = upload(c, c->d.eb0, e0)) || (rc = upload(c, c->d.eb1, e1)))
+    return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return 0;
+}
+
+Par make_par(const gks2l_ctx *c) {
+  Par p;
+  p.g = c->par.g; p.chi = c->par.chi; p.cfl = c->par.cfl;
+  p.eps = c->par.eps; p.eps_num = c->par.eps_num;
+  p.gam_hi = c->par.weno_gamma_hi; p.weno_eps = c->par.weno_eps;
+  p.t_end = 0;
+  p.use_gate = c->par.indicator == GKS2L_INDICATOR_MLP ? 1 : 0;
+  return p;
+}
+
+inline unsigned blocks(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
+
+template <typename R>
+void launch_stage(gks2l_ctx *c, int stage) {
+  const Dev &d = c->d;
+  Par p = make_par(c);
+  k_recon<R><<<blocks(d.nt, 32), dim3(32, 6), 0, c->stream>>>(d, p);
+  k_iface<R><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d);
+  k_edge<R><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d, p, stage);
+  k_update<<<blocks(d.nt, 128), 128, 0, c->stream>>>(d, p, stage);
+}
+
+void launch_stage_any(gks2l_ctx *c, int stage) {
+  if (c->par.precision == GKS2L_FP32) launch_stage<float>(c, stage);
+  else launch_stage<double>(c, stage);
+}
+
+void launch_step_begin(gks2l_ctx *c) {
+  Par p = make_par(c);
+  k_step_begin<<<blocks(c->d.ninst, 128), 128, 0, c->stream>>>(c->d, p, c->d_tend);
+}
+
+void drop_graph(gks2l_ctx *c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+}
+
+int ensure_graph(gks2l_ctx *c) {
+  if (c->gexec || !c->stream) return 0;
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  launch_step_begin(c);
+  launch_stage_any(c, 1);
+  launch_stage_any(c, 2);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &c->graph);
+  if (e != cudaSuccess) {
+    c->err = std::string("graph capture: ") + cudaGetErrorString(e);
+    c->graph = nullptr;
+    return GKS2L_ECUDA;
+  }
+  CK(cudaGraphInstantiate(&c->gexec, c->graph, 0));
+  return 0;
+}
+
+int check_status(gks2l_ctx *c) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, c->d.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (st & 2) return GKS2L_ENONFINITE;
+  if (st & 1) return GKS2L_ENEGDEPTH;
+  return 0;
+}
+
+int after_state(gks2l_ctx *c) {
+  Par p = make_par(c);
+  k_reset_stats<<<blocks(c->d.ninst, 128), 128, 0, c->stream>>>(c->d);
+  CK(cudaMemsetAsync(c->d.t, 0, sizeof(double) * c->d.ninst, c->stream));
+  CK(cudaMemsetAsync(c->d.dt, 0, sizeof(double) * c->d.ninst, c->stream));
+  CK(cudaMemsetAsync(c->d.status, 0, sizeof(int), c->stream));
+  k_cfl<<<blocks(c->d.nt, 128), 128, 0, c->stream>>>(c->d, p);
+  CK(cudaGetLastError());
+  c->phase = 0;
+  c->stages = 0;
+  c->has_state = true;
+  return 0;
+}
+
+int create_impl(int n, const gks2l_mesh *meshes, const gks2l_params *params, gks2l_ctx **out) {
+  if (!meshes || !out || n <= 0) return GKS2L_EINVAL;
+  gks2l_ctx *c = new gks2l_ctx();
+  if (params) c->par = *params;
+  else gks2l_default_params(&c->par);
+  if (!(c->par.g > 0) || !(c->par.cfl > 0) || !(c->par.eps > 0) || c->par.eps_num < 0 || !(c->par.chi > 0) ||
+      !(c->par.weno_gamma_hi > 0 && c->par.weno_gamma_hi <= 1) || c->par.weno_eps < 0 ||
+      (c->par.precision != GKS2L_FP64 && c->par.precision != GKS2L_FP32)) {
+    delete c;
+    return GKS2L_EINVAL;
+  }
+  c->rsize = c->par.precision == GKS2L_FP32 ? 4 : 8;
+  int rc = prepare(n, meshes, c->prep, c->err);
+  if (rc) {
+    fprintf(stderr, "gks2l: %s\n", c->err.c_str());
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return GKS2L_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gks2l_default_params(gks2l_params *p) {
+  if (!p) return GKS2L_EINVAL;
+  p->g = 9.81;
+  p->chi = 1.0;
+  p->cfl = 0.5;
+  p->eps = 0.05;
+  p->eps_num = 5.0;
+  p->weno_gamma_hi = 0.85;
+  p->weno_eps = 1.0;
+  p->precision = GKS2L_FP64;
+  p->indicator = GKS2L_INDICATOR_OFF;
+  p->indicator_threshold = 0.5f;
+  return GKS2L_OK;
+}
+
+int gks2l_create(const gks2l_mesh *mesh, const gks2l_params *params, gks2l_ctx **out) {
+  return create_impl(1, mesh, params, out);
+}
+
+int gks2l_create_ensemble(int32_t n, const gks2l_mesh *meshes, const gks2l_params *params, gks2l_ctx **out) {
+  return create_impl(n, meshes, params, out);
+}
+
+int gks2l_workspace_bytes(const gks2l_ctx *ctx, size_t *bytes) {
+  if (!ctx || !bytes) return GKS2L_EINVAL;
+  gks2l_ctx tmp;
+  tmp.prep.nt = ctx->prep.nt;
+  tmp.prep.ne = ctx->prep.ne;
+  tmp.prep.ninst = ctx->prep.ninst;
+  tmp.rsize = ctx->rsize;
+  *bytes = layout(&tmp, nullptr);
+  return GKS2L_OK;
+}
+
+int gks2l_bind(gks2l_ctx *c, void *d_workspace, size_t bytes, void *stream) {
+  if (!c || !d_workspace) return GKS2L_EINVAL;
+  if (((uintptr_t)d_workspace & 255) != 0) return GKS2L_EINVAL;
+  size_t need = layout(c, nullptr);
+  if (bytes < need) return GKS2L_ESPACE;
+  drop_graph(c);
+  c->ws = (char *)d_workspace;
+  c->ws_bytes = bytes;
+  c->stream = (cudaStream_t)stream;
+  layout(c, c->ws);
+  const Prep &P = c->prep;
+  std::vector<double> ia(P.nt);
+  for (int j = 0; j < P.nt; j++) ia[j] = 1.0 / P.area[j];
+  std::vector<double> xf(4 * kMaxXf, 0.0);
+  std::copy(P.xf.begin(), P.xf.end(), xf.begin());
+  int rc;
+  if ((rc = upload(c, c->d.inst, P.inst)) || (rc = upload(c, c->d.inv_area, ia)) ||
+      (rc = upload(c, c->d.area, P.area)) || (rc = upload(c, c->d.hs, P.hs)) || (rc = upload(c, c->d.dX, P.dX)) ||
+      (rc = upload(c, c->d.st_cell, P.st_cell)) || (rc = upload(c, c->d.st_xf, P.st_xf)) ||
+      (rc = upload(c, c->d.plane, P.plane)) || (rc = upload(c, c->d.cedge, P.cedge)) ||
+      (rc = upload(c, c->d.inst_first, P.inst_first)) || (rc = upload(c, c->d.eL, P.eL)) ||
+      (rc = upload(c, c->d.eR, P.eR)) || (rc = upload(c, c->d.exf, P.exf)) || (rc = upload(c, c->d.en0, P.en0)) ||
+      (rc = upload(c, c->d.en1, P.en1)) || (rc = upload(c, c->d.elen, P.elen)) || (rc = upload(c, c->d.xf, xf)) ||
+      (rc = upload(c, c->d_perm, P.perm)))
+    return rc;
+  if (c->rsize == 4) {
+    std::vector<float> t1, t2, t3, t4, t5, t6;
+    if ((rc = upload_r(c, c->d.lsq, P.lsq, t1)) || (rc = upload_r(c, c->d.p1op, P.p1op, t2)) ||
+        (rc = upload_r(c, c->d.bq, P.bq, t3)) || (rc = upload_r(c, c->d.mmean, P.mmean, t4)) ||
+        (rc = upload_r(c, c->d.exiL, P.exiL, t5)) || (rc = upload_r(c, c->d.exiR, P.exiR, t6)))
+      return rc;
+    CK(cudaStreamSynchronize(c->stream));
+  } else {
+    if ((rc = upload(c, c->d.lsq, P.lsq)) || (rc = upload(c, c->d.p1op, P.p1op)) || (rc = upload(c, c->d.bq, P.bq)) ||
+        (rc = upload(c, c->d.mmean, P.mmean)) || (rc = upload(c, c->d.exiL, P.exiL)) ||
+        (rc = upload(c, c->d.exiR, P.exiR)))
+      return rc;
+  }
+  CK(cudaMemsetAsync(c->d.gate, 0, P.nt, c->stream));
+  CK(cudaMemsetAsync(c->d.gate_count, 0, 2 * sizeof(unsigned long long), c->stream));
+  CK(cudaMemsetAsync(c->d.status, 0, sizeof(int), c->stream));
+  c->bound = true;
+  c->has_state = false;
+  return upload_bathymetry(c);
+}
+
+int gks2l_set_bathymetry(gks2l_ctx *c, const double *b_vert) {
+  if (!c || !b_vert) return GKS2L_EINVAL;
+  c->bvert.assign(b_vert, b_vert + c->prep.nv);
+  c->has_b = true;
+  if (c->bound) return upload_bathymetry(c);
+  return GKS2L_OK;
+}
+
+int gks2l_set_state(gks2l_ctx *c, const double *avg, const double *grad) {
+  if (!c || !avg) return GKS2L_EINVAL;
+  if (!c->bound) return GKS2L_ESTATE;
+  const size_t nt = c->prep.nt;
+  CK(cudaMemcpyAsync(c->d_stage, avg, 6 * nt * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (grad) CK(cudaMemcpyAsync(c->d_stage + 6 * nt, grad, 12 * nt * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  k_gather<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 6, c->d_perm, c->d_stage, c->d.avg);
+  k_gather<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 12, c->d_perm, grad ? c->d_stage + 6 * nt : nullptr,
+                                                  c->d.grad);
+  CK(cudaGetLastError());
+  int rc = after_state(c);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));   // the host arrays may be released after return
+  return GKS2L_OK;
+}
+
+int gks2l_set_state_device(gks2l_ctx *c, const double *d_avg, const double *d_grad) {
+  if (!c || !d_avg) return GKS2L_EINVAL;
+  if (!c->bound) return GKS2L_ESTATE;
+  const size_t nt = c->prep.nt;
+  k_gather<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 6, c->d_perm, d_avg, c->d.avg);
+  k_gather<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 12, c->d_perm, d_grad, c->d.grad);
+  CK(cudaGetLastError());
+  return after_state(c);
+}
+
+int gks2l_advance(gks2l_ctx *c, int32_t n_stages, double t_end, double *t_out) {
+  if (!c || n_stages < 0) return GKS2L_EINVAL;
+  if (!c->bound || !c->has_state) return GKS2L_ESTATE;
+  CK(cudaMemcpyAsync(c->d_tend, &t_end, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  int left = n_stages;
+  if (left > 0 && c->phase == 1) {
+    launch_stage_any(c, 2);
+    c->phase = 0;
+    left--;
+    c->stages++;
+  }
+  int steps = left / 2;
+  if (steps > 0) {
+    int rc = ensure_graph(c);
+    if (rc) return rc;
+    for (int s = 0; s < steps; s++) {
+      if (c->gexec) {
+        CK(cudaGraphLaunch(c->gexec, c->stream));
+      } else {
+        launch_step_begin(c);
+        launch_stage_any(c, 1);
+        launch_stage_any(c, 2);
+      }
+    }
+    c->stages += 2 * steps;
+  }
+  if (left % 2) {
+    launch_step_begin(c);
+    launch_stage_any(c, 1);
+    c->phase = 1;
+    c->stages++;
+  }
+  CK(cudaGetLastError());
+  if (t_out) {
+    CK(cudaMemcpyAsync(t_out, c->d.t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return check_status(c);
+  }
+  return GKS2L_OK;
+}
+
+int gks2l_get_state(gks2l_ctx *c, double *avg, double *grad) {
+  if (!c || !avg) return GKS2L_EINVAL;
+  if (!c->bound || !c->has_state) return GKS2L_ESTATE;
+  const size_t nt = c->prep.nt;
+  k_scatter<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 6, c->d_perm, c->d.avg, c->d_stage);
+  k_scatter<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 12, c->d_perm, c->d.grad, c->d_stage + 6 * nt);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(avg, c->d_stage, 6 * nt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (grad) CK(cudaMemcpyAsync(grad, c->d_stage + 6 * nt, 12 * nt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return GKS2L_OK;
+}
+
+int gks2l_get_state_device(gks2l_ctx *c, double *d_avg, double *d_grad) {
+  if (!c || !d_avg) return GKS2L_EINVAL;
+  if (!c->bound || !c->has_state) return GKS2L_ESTATE;
+  const size_t nt = c->prep.nt;
+  k_scatter<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 6, c->d_perm, c->d.avg, d_avg);
+  if (d_grad) k_scatter<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 12, c->d_perm, c->d.grad, d_grad);
+  CK(cudaGetLastError());
+  return GKS2L_OK;
+}
+
+int gks2l_stats(gks2l_ctx *c, gks2l_stats_t *out) {
+  if (!c || !out) return GKS2L_EINVAL;
+  if (!c->bound || !c->has_state) return GKS2L_ESTATE;
+  std::vector<double> mass(2 * c->prep.ninst);
+  double t = 0, dt = 0;
+  int st = 0;
+  unsigned long long cnt[2] = {0, 0};
+  CK(cudaMemcpyAsync(mass.data(), c->d.mass, mass.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&t, c->d.t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&dt, c->d.dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&st, c->d.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(cnt, c->d.gate_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  out->mass[0] = out->mass[1] = 0;
+  for (int i = 0; i < c->prep.ninst; i++) {
+    out->mass[0] += mass[2 * i];
+    out->mass[1] += mass[2 * i + 1];
+  }
+  out->t = t;
+  out->dt_last = dt;
+  out->stages_done = c->stages;
+  out->status = (st & 2) ? GKS2L_ENONFINITE : (st & 1) ? GKS2L_ENEGDEPTH : 0;
+  out->n_instances = c->prep.ninst;
+  out->smooth_fraction = cnt[1] ? (double)cnt[0] / (double)cnt[1] : 0.0;
+  return GKS2L_OK;
+}
+
+int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[5]) {
+  if (!c || !ms || n_steps <= 0) return GKS2L_EINVAL;
+  if (!c->bound || !c->has_state || c->phase != 0) return GKS2L_ESTATE;
+  double zero = 0.0;
+  CK(cudaMemcpyAsync(c->d_tend, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  cudaEvent_t ev[10];
+  for (int i = 0; i < 10; i++) CK(cudaEventCreate(&ev[i]));
+  double acc[5] = {0, 0, 0, 0, 0};
+  const Dev &d = c->d;
+  Par p = make_par(c);
+  const bool f32 = c->par.precision == GKS2L_FP32;
+  for (int s = 0; s < n_steps; s++) {
+    CK(cudaEventRecord(ev[0], c->stream));
+    launch_step_begin(c);
+    CK(cudaEventRecord(ev[1], c->stream));
+    for (int stage = 1; stage <= 2; stage++) {
+      CK(cudaEventRecord(ev[2], c->stream));
+      if (f32) k_recon<float><<<blocks(d.nt, 32), dim3(32, 6), 0, c->stream>>>(d, p);
+      else k_recon<double><<<blocks(d.nt, 32), dim3(32, 6), 0, c->stream>>>(d, p);
+      CK(cudaEventRecord(ev[3], c->stream));
+      if (f32) k_iface<float><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d);
+      else k_iface<double><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d);
+      CK(cudaEventRecord(ev[4], c->stream));
+      if (f32) k_edge<float><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d, p, stage);
+      else k_edge<double><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d, p, stage);
+      CK(cudaEventRecord(ev[5], c->stream));
+      k_update<<<blocks(d.nt, 128), 128, 0, c->stream>>>(d, p, stage);
+      CK(cudaEventRecord(ev[6], c->stream));
+      CK(cudaEventSynchronize(ev[6]));
+      float t;
+      for (int k = 0; k < 4; k++) {
+        CK(cudaEventElapsedTime(&t, ev[2 + k], ev[3 + k]));
+        acc[k] += t;
+      }
+    }
+    float t0;
+    CK(cudaEventElapsedTime(&t0, ev[0], ev[1]));
+    acc[4] += t0;
+  }
+  CK(cudaGetLastError());
+  for (int i = 0; i < 10; i++) cudaEventDestroy(ev[i]);
+  for (int k = 0; k < 4; k++) ms[k] = acc[k] / (2.0 * n_steps);
+  ms[4] = acc[4] / n_steps;
+  c->stages += 2 * n_steps;
+  return GKS2L_OK;
+}
+
+int gks2l_set_mlp(gks2l_ctx *c, const float *params, size_t n_floats) {
+  (void)c; (void)params; (void)n_floats;
+  return GKS2L_ENOTIMPL;
+}
+
+int gks2l_harvest(gks2l_ctx *c, float tol, float *d_features, float *d_labels) {
+  (void)c; (void)tol; (void)d_features; (void)d_labels;
+  return GKS2L_ENOTIMPL;
+}
+
+const char *gks2l_error_string(int code) {
+  switch (code) {
+    case GKS2L_OK: return "ok";
+    case GKS2L_EINVAL: return "invalid argument";
+    case GKS2L_EMESH: return "mesh not usable";
+    case GKS2L_ECUDA: return "CUDA runtime error";
+    case GKS2L_ESTATE: return "call out of order";
+    case GKS2L_ENEGDEPTH: return "non-positive depth";
+    case GKS2L_ENONFINITE: return "non-finite value";
+    case GKS2L_ESPACE: return "workspace too small";
+    case GKS2L_ENOTIMPL: return "not implemented";
+    default: return "unknown status";
+  }
+}
+
+void gks2l_destroy(gks2l_ctx *c) {
+  if (!c) return;
+  drop_graph(c);
+  delete c;
+}
+
+}  // extern "C"

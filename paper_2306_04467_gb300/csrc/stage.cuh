@@ -1,0 +1,670 @@
+// Per-thread work of one S2O4 stage of the compact two-layer GKS
+// (arXiv 2306.04467), shared by the CUDA kernels in gks2l.cu. Each function
+// handles one unit of work (a cell-variable, an edge Gauss point of one layer,
+// or a cell) and is written as plain host/device code so the arithmetic of a
+// unit does not depend on the launch shape.
+//
+// Precision: `R` is the type of the deviation arithmetic (double in the FP64
+// form, float in the FP32 form). Cell averages, depths at Gauss points,
+// the hydrostatic parts of the interface solution and every flux/source sum
+// stay in double in both forms, which keeps the rest state exact
+// (Sec. 3.2: balance between the interface flux and the cell sources).
+#pragma once
+#include <cmath>
+#include <cstdint>
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#define __forceinline__ inline
+#endif
+
+namespace gks2l {
+
+#ifndef __CUDACC__
+using std::isfinite;
+#endif
+
+constexpr int NV = 6;        // h2, h2U2, h2V2, h1 (reconstructed as eta1 = h1 + B), h1U1, h1V1
+constexpr int NSLOT = 9;
+constexpr int NCOL = 17;
+constexpr int NCOEF = 10;    // per variable: c0 (value offset) + 9 Taylor coefficients
+
+// Device view of the workspace. R-typed arrays are stored as void* and cast.
+struct Dev {
+  int nt, ne, ninst;
+  // per cell
+  const int *inst;
+  const double *inv_area, *area, *hs, *dX;
+  const double *bmean, *bgx, *bgy;
+  const int *st_cell;
+  const int8_t *st_xf;
+  const void *lsq, *p1op, *bq, *mmean;
+  const double *plane;
+  const int *cedge;
+  const int *inst_first;
+  double *avg, *grad;       // state [v][cell], [(v*2+d)][cell]
+  double *Wn, *Ln, *Ltn;    // stage snapshot
+  void *coef;               // reconstruction deviations [v*10+k][cell]
+  void *omg;                // omega_H / gamma_H of eta1 [0] and h2 [1], type R
+  uint8_t *gate;            // 1 = smooth by the learned indicator
+  // per edge
+  const int *eL, *eR;
+  const int8_t *exf;
+  const double *en0, *en1, *elen, *eb0, *eb1;
+  const void *exiL, *exiR;  // [4][edge]
+  double *hc;               // [2][edge]: edge-centre eta1-hat, h2-hat
+  double *eF, *eFt, *eW, *eWt, *eWn;  // [6][edge], Gauss-point sums (weights 1/2)
+  // per instance
+  double *dt, *t;
+  unsigned long long *dtbits;
+  double *mass;             // [inst*2 + layer]
+  int *status;
+  unsigned long long *gate_count;
+  const double *xf;         // [code*4] 2x2 linear parts of image transforms
+};
+
+struct Par {
+  double g, chi, cfl, eps, eps_num, gam_hi, weno_eps, t_end;
+  int use_gate;
+};
+
+template <typename R> __host__ __device__ __forceinline__ R r_erf(R x);
+template <> __host__ __device__ __forceinline__ double r_erf<double>(double x) { return erf(x); }
+template <> __host__ __device__ __forceinline__ float r_erf<float>(float x) { return erff(x); }
+template <typename R> __host__ __device__ __forceinline__ R r_erfc(R x);
+template <> __host__ __device__ __forceinline__ double r_erfc<double>(double x) { return erfc(x); }
+template <> __host__ __device__ __forceinline__ float r_erfc<float>(float x) { return erfcf(x); }
+template <typename R> __host__ __device__ __forceinline__ R r_exp(R x);
+template <> __host__ __device__ __forceinline__ double r_exp<double>(double x) { return exp(x); }
+template <> __host__ __device__ __forceinline__ float r_exp<float>(float x) { return expf(x); }
+template <typename R> __host__ __device__ __forceinline__ R r_expm1(R x);
+template <> __host__ __device__ __forceinline__ double r_expm1<double>(double x) { return expm1(x); }
+template <> __host__ __device__ __forceinline__ float r_expm1<float>(float x) { return expm1f(x); }
+template <typename R> __host__ __device__ __forceinline__ R r_sqrt(R x);
+template <> __host__ __device__ __forceinline__ double r_sqrt<double>(double x) { return sqrt(x); }
+template <> __host__ __device__ __forceinline__ float r_sqrt<float>(float x) { return sqrtf(x); }
+
+template <typename R>
+__host__ __device__ __forceinline__ void monos(R x, R y, R m[10], R mx[10], R my[10]) {
+  const R h = (R)0.5, s = (R)(1.0 / 6.0);
+  R xx = x * x, yy = y * y, xy = x * y;
+  m[0] = 1; m[1] = x; m[2] = y; m[3] = h * xx; m[4] = xy; m[5] = h * yy;
+  m[6] = xx * x * s; m[7] = h * xx * y; m[8] = h * x * yy; m[9] = yy * y * s;
+  mx[0] = 0; mx[1] = 1; mx[2] = 0; mx[3] = x; mx[4] = y; mx[5] = 0;
+  mx[6] = h * xx; mx[7] = xy; mx[8] = h * yy; mx[9] = 0;
+  my[0] = 0; my[1] = 0; my[2] = 1; my[3] = 0; my[4] = x; my[5] = y;
+  my[6] = 0; my[7] = h * xx; my[8] = xy; my[9] = h * yy;
+}
+
+// ------------------------------------------------------------------ cell data
+// Average of reconstructed variable v of cell c seen through transform code xf
+// (variables: h2, m2x, m2y, eta1 = h1 + B, m1x, m1y).
+__host__ __device__ __forceinline__ double img_avg(const Dev &d, int v, int c, int xf) {
+  const int N = d.nt;
+  if (v == 0) return d.avg[c];
+  if (v == 3) return d.avg[3 * N + c] + d.bmean[c];
+  int b = v < 3 ? 1 : 4;
+  double mx = d.avg[b * N + c], my = d.avg[(b + 1) * N + c];
+  if (xf == 0) return v == b ? mx : my;
+  const double *M = d.xf + 4 * xf;
+  return v == b ? M[0] * mx + M[1] * my : M[2] * mx + M[3] * my;
+}
+__host__ __device__ __forceinline__ void img_grad(const Dev &d, int v, int c, int xf, double g[2]) {
+  const int N = d.nt;
+  const double *G = d.grad;
+  if (v == 0 || v == 3) {
+    double gx = G[(2 * v) * N + c], gy = G[(2 * v + 1) * N + c];
+    if (v == 3) { gx += d.bgx[c]; gy += d.bgy[c]; }
+    if (xf == 0) { g[0] = gx; g[1] = gy; return; }
+    const double *M = d.xf + 4 * xf;
+    g[0] = M[0] * gx + M[1] * gy;
+    g[1] = M[2] * gx + M[3] * gy;
+    return;
+  }
+  int b = v < 3 ? 1 : 4;
+  int row = v - b;
+  if (xf == 0) {
+    g[0] = G[(2 * v) * N + c];
+    g[1] = G[(2 * v + 1) * N + c];
+    return;
+  }
+  // momentum gradient tensor T_ik = d m_i / d x_k -> M T M^T
+  double T[2][2] = {{G[(2 * b) * N + c], G[(2 * b + 1) * N + c]},
+                    {G[(2 * b + 2) * N + c], G[(2 * b + 3) * N + c]}};
+  const double *M = d.xf + 4 * xf;
+  double Mr[2] = {M[2 * row], M[2 * row + 1]};
+  for (int k = 0; k < 2; k++) {
+    double s = 0;
+    for (int a = 0; a < 2; a++)
+      for (int b2 = 0; b2 < 2; b2++) s += Mr[a] * T[a][b2] * M[2 * k + b2];
+    g[k] = s;
+  }
+}
+
+// --------------------------------------------------- compact reconstruction
+// One cell and one variable: P3 least squares (Eq. Recons-system), three P1
+// candidates on {cell, face neighbour}, smoothness indicators and WENO-Z
+// weights, combined polynomial written as deviations in the Taylor basis.
+template <typename R>
+__host__ __device__ inline void recon_unit(const Dev &d, const Par &p, int j, int v) {
+  const int N = d.nt;
+  const R *lsq = (const R *)d.lsq;
+  const R *p1 = (const R *)d.p1op;
+  const R *bq = (const R *)d.bq;
+  const R *mm = (const R *)d.mmean;
+  R *coef = (R *)d.coef;
+  const double q0 = img_avg(d, v, j, 0);
+  const double hs = d.hs[j];
+  R rhs[NCOL];
+  for (int s = 0; s < NSLOT; s++) {
+    int c = d.st_cell[s * N + j];
+    rhs[s] = c >= 0 ? (R)(img_avg(d, v, c, d.st_xf[s * N + j]) - q0) : (R)0;
+  }
+  double g[2];
+  img_grad(d, v, j, 0, g);
+  rhs[9] = (R)(hs * g[0]);
+  rhs[10] = (R)(hs * g[1]);
+  for (int f = 0; f < 3; f++) {
+    img_grad(d, v, d.st_cell[f * N + j], d.st_xf[f * N + j], g);
+    rhs[11 + 2 * f] = (R)(hs * g[0]);
+    rhs[12 + 2 * f] = (R)(hs * g[1]);
+  }
+  R a[9];
+  for (int r = 0; r < 9; r++) {
+    R s = 0;
+    for (int c = 0; c < NCOL; c++) s += lsq[(r * NCOL + c) * N + j] * rhs[c];
+    a[r] = s;
+  }
+  const R gh = (R)p.gam_hi, gl = (R)((1.0 - p.gam_hi) / 3.0);
+  R fac = 1, wf[3] = {gl, gl, gl}, b[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  const bool linear = p.use_gate && d.gate[j];
+  if (!linear) {
+    R beta[4];
+    for (int f = 0; f < 3; f++) {
+      R r5[5] = {rhs[f], rhs[9], rhs[10], rhs[11 + 2 * f], rhs[12 + 2 * f]};
+      for (int k = 0; k < 2; k++) {
+        R s = 0;
+        for (int c = 0; c < 5; c++) s += p1[((f * 2 + k) * 5 + c) * N + j] * r5[c];
+        b[f][k] = s;
+      }
+      beta[1 + f] = b[f][0] * b[f][0] + b[f][1] * b[f][1];
+    }
+    R bh = 0;
+    int idx = 0;
+    for (int k = 0; k < 9; k++)
+      for (int l = k; l < 9; l++) bh += bq[(idx++) * N + j] * a[k] * a[l];
+    beta[0] = bh;
+    R tz = (fabs(bh - beta[1]) + fabs(bh - beta[2]) + fabs(bh - beta[3])) * (R)(1.0 / 3.0);
+    R eps = (R)(p.weno_eps * d.area[j] * (1.0 + q0 * q0));
+    R w[4], ws = 0;
+    const R gam[4] = {gh, gl, gl, gl};
+    for (int k = 0; k < 4; k++) {
+      R r = tz / (beta[k] + eps);
+      w[k] = gam[k] * (1 + r * r);
+      ws += w[k];
+    }
+    R iw = 1 / ws;
+    fac = w[0] * iw / gh;
+    for (int f = 0; f < 3; f++) wf[f] = w[1 + f] * iw;
+  }
+  // R = (w_H / g_H)(P3 - sum g_m P1_m) + sum w_m P1_m
+  R r[10];
+  for (int k = 1; k < 10; k++) r[k] = fac * a[k - 1];
+  for (int f = 0; f < 3; f++) {
+    R cf = wf[f] - fac * gl;
+    r[1] += cf * b[f][0];
+    r[2] += cf * b[f][1];
+  }
+  R c0 = 0;
+  for (int k = 3; k < 10; k++) c0 -= r[k] * mm[(k - 3) * N + j];
+  r[0] = c0;
+  for (int k = 0; k < 10; k++) coef[(v * NCOEF + k) * N + j] = r[k];
+  if (v == 3) ((R *)d.omg)[j] = fac;
+  if (v == 0) ((R *)d.omg)[N + j] = fac;
+}
+
+// ------------------------------------------------- evaluation at an edge point
+// Edge-point side data for layer ell (0: lower, reconstructed eta1; 1: upper).
+// Depth and level are double (cell average + polynomial deviation); the
+// discharge, velocities and all gradients are type R.
+template <typename R> struct SideVals {
+  double h;       // depth at the point
+  double lev;     // level variable: eta1 (lower) or h2 (upper)
+  R mx, my;       // discharge
+  R gh[2];        // gradient of the depth
+  R glev[2];      // gradient of the level variable
+  R gm[2][2];     // discharge gradient tensor d m_i / d x_k
+  R goth[2];      // gradient of the other layer's level variable
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ void rot2(const double *M, R v[2]) {
+  R a = v[0], b = v[1];
+  v[0] = (R)M[0] * a + (R)M[1] * b;
+  v[1] = (R)M[2] * a + (R)M[3] * b;
+}
+
+// Values and gradients of the layer's variables and the other layer's level
+// gradient for cell c at scaled point (x, y), seen through transform xf.
+template <typename R>
+__host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, R x, R y, double bq,
+                                          SideVals<R> &s) {
+  const int N = d.nt;
+  const R *coef = (const R *)d.coef;
+  const int v0 = ell == 0 ? 3 : 0, vo = ell == 0 ? 0 : 3;
+  R m[10], mx[10], my[10];
+  monos<R>(x, y, m, mx, my);
+  const R ih = (R)(1.0 / d.hs[c]);
+  R dev[3], gx[4], gy[4];
+  for (int i = 0; i < 4; i++) {
+    int v = i < 3 ? v0 + i : vo;
+    R a = 0, ax = 0, ay = 0;
+    for (int k = 0; k < 10; k++) {
+      R ck = coef[(v * NCOEF + k) * N + c];
+      a += ck * m[k];
+      ax += ck * mx[k];
+      ay += ck * my[k];
+    }
+    if (i < 3) dev[i] = a;
+    gx[i] = ax * ih;
+    gy[i] = ay * ih;
+  }
+  R gb[2] = {0, 0};
+  if (ell == 0) {
+    gb[0] = (R)d.bgx[c];
+    gb[1] = (R)d.bgy[c];
+    const double a3 = d.avg[3 * N + c];
+    s.h = a3 + (d.bmean[c] - bq) + (double)dev[0];   // h1 = eta1 - B(x)
+    s.lev = (a3 + d.bmean[c]) + (double)dev[0];
+  } else {
+    s.h = d.avg[c] + (double)dev[0];
+    s.lev = s.h;
+  }
+  s.mx = (R)(d.avg[(v0 + 1) * N + c] + (double)dev[1]);
+  s.my = (R)(d.avg[(v0 + 2) * N + c] + (double)dev[2]);
+  s.glev[0] = gx[0]; s.glev[1] = gy[0];
+  s.gm[0][0] = gx[1]; s.gm[0][1] = gy[1];
+  s.gm[1][0] = gx[2]; s.gm[1][1] = gy[2];
+  s.goth[0] = gx[3]; s.goth[1] = gy[3];
+  if (xf != 0) {
+    const double *M = d.xf + 4 * xf;
+    R mv[2] = {s.mx, s.my};
+    rot2<R>(M, mv);
+    s.mx = mv[0]; s.my = mv[1];
+    rot2<R>(M, s.glev);
+    rot2<R>(M, s.goth);
+    rot2<R>(M, gb);
+    R T[2][2] = {{s.gm[0][0], s.gm[0][1]}, {s.gm[1][0], s.gm[1][1]}};
+    for (int i2 = 0; i2 < 2; i2++)
+      for (int k = 0; k < 2; k++) {
+        R acc = 0;
+        for (int a = 0; a < 2; a++)
+          for (int b2 = 0; b2 < 2; b2++) acc += (R)M[2 * i2 + a] * T[a][b2] * (R)M[2 * k + b2];
+        s.gm[i2][k] = acc;
+      }
+  }
+  s.gh[0] = s.glev[0] - gb[0];
+  s.gh[1] = s.glev[1] - gb[1];
+}
+
+// ------------------------------------------------ gas-kinetic interface solution
+template <typename R> struct Kern {
+  R gu, gv, puu, puv, pvv, bu, bv;
+};
+
+// Central moments mu_k = <c^k> (k = 0..5, c = u - U) of the normalised 1-D
+// Maxwellian over the half line sgn*u > 0; e0 = mu_0 - 1/2, E = e^{-lam U^2}/(2 sqrt(pi lam)).
+template <typename R>
+__host__ __device__ __forceinline__ void half_moments(R U, R lam, R sgn, R mu[6], R &e0, R &E) {
+  const R th = (R)0.5 / lam;
+  e0 = sgn * (R)0.5 * r_erf<R>(r_sqrt<R>(lam) * U);
+  E = r_exp<R>(-lam * U * U) * (R)0.5 / r_sqrt<R>((R)3.14159265358979323846 * lam);
+  mu[0] = (R)0.5 + e0;
+  mu[1] = sgn * E;
+  R pw = -sgn * U * E;
+  mu[2] = th * mu[0] + pw;
+  pw *= -U;
+  mu[3] = 2 * th * mu[1] + pw;
+  pw *= -U;
+  mu[4] = 3 * th * mu[2] + pw;
+  pw *= -U;
+  mu[5] = 4 * th * mu[3] + pw;
+}
+
+// Slope + force kernel on a Maxwellian base (h, U, V, lam), written as a
+// polynomial in c = u - U: the exact derivative of ln g along n and t, plus
+// the force term, whose cubic part combines into (lam/h) |c|^2 (D . c) with
+// D = grad h - grad Phi / G (local frame).
+template <typename R>
+__host__ __device__ __forceinline__ Kern<R> make_kern(R h, R U, R V, R lam, const R dn[3], const R dt[3],
+                                                      const R D[2]) {
+  Kern<R> K;
+  R ih = 1 / h;
+  R aun = (dn[1] - U * dn[0]) * ih, avn = (dn[2] - V * dn[0]) * ih;
+  R aut = (dt[1] - U * dt[0]) * ih, avt = (dt[2] - V * dt[0]) * ih;
+  R al = lam * ih * (dn[0] * U + dt[0] * V);
+  R tl = 2 * lam;
+  K.gu = tl * (aun * U + aut * V);
+  K.gv = tl * (avn * U + avt * V);
+  K.puu = al + tl * aun;
+  K.pvv = al + tl * avt;
+  K.puv = tl * (avn + aut);
+  K.bu = lam * ih * D[0];
+  K.bv = lam * ih * D[1];
+  return K;
+}
+
+// moments of the kernel with weights (1, u, v) and (u, u^2, uv), per unit density
+template <typename R>
+__host__ __device__ __forceinline__ void kern_moments(const Kern<R> &K, const R mu[6], R th, R U, R V, R out[6]) {
+  const R n2 = th, n4 = 3 * th * th;
+  R T00 = K.gu * mu[1] + K.puu * mu[2] + K.pvv * mu[0] * n2 + K.bu * (mu[3] + mu[1] * n2);
+  R T10 = K.gu * mu[2] + K.puu * mu[3] + K.pvv * mu[1] * n2 + K.bu * (mu[4] + mu[2] * n2);
+  R T20 = K.gu * mu[3] + K.puu * mu[4] + K.pvv * mu[2] * n2 + K.bu * (mu[5] + mu[3] * n2);
+  R T01 = K.gv * mu[0] * n2 + K.puv * mu[1] * n2 + K.bv * (mu[2] * n2 + mu[0] * n4);
+  R T11 = K.gv * mu[1] * n2 + K.puv * mu[2] * n2 + K.bv * (mu[3] * n2 + mu[1] * n4);
+  out[0] = T00;
+  out[1] = U * T00 + T10;
+  out[2] = V * T00 + T01;
+  out[3] = out[1];
+  out[4] = U * U * T00 + 2 * U * T10 + T20;
+  out[5] = U * V * T00 + V * T10 + U * T01 + T11;
+}
+
+// time integrals over [0, delta] of C1..C5
+template <typename R>
+__host__ __device__ __forceinline__ void time_ints(R tau, R delta, R q[5]) {
+  R x = delta / tau;
+  R em = -r_expm1<R>(-x);
+  R e = r_exp<R>(-x);
+  q[0] = delta - tau * em;
+  q[1] = -tau * delta * (1 + e) + 2 * tau * tau * em;
+  q[2] = (R)0.5 * delta * delta - tau * delta + tau * tau * em;
+  q[3] = tau * em;
+  q[4] = tau * delta * e - tau * tau * em;
+}
+
+// One layer at one Gauss point, local frame (x along the normal from L to R).
+// Returns the value and time derivative at the stage start of the flux F and
+// of the interface variables W (fit of the two time integrals over delta and
+// delta/2). The hydrostatic parts (h_b and G h_b^2 / 2, h_b = (h_l + h_r)/2)
+// are added in double; everything else is a deviation of type R.
+template <typename R>
+__host__ __device__ inline void gks_layer(double hl, double hr, R Ul, R Vl, R Ur, R Vr, const R dnl[3],
+                                          const R dtl[3], const R Dl[2], const R dnr[3], const R dtr[3],
+                                          const R Dr[2], double G, double tau, double delta, double F[3],
+                                          double Ft[3], double W[3], double Wt[3]) {
+  const R g = (R)G;
+  const R hlR = (R)hl, hrR = (R)hr;
+  const R laml = 1 / (g * hlR), lamr = 1 / (g * hrR);
+  const R thl = (R)0.5 * g * hlR, thr = (R)0.5 * g * hrR;
+  R mul[6], mur[6], e0l, e0r, El, Er;
+  half_moments<R>(Ul, laml, (R)1, mul, e0l, El);
+  half_moments<R>(Ur, lamr, (R)-1, mur, e0r, Er);
+  // W-bar: the t = 0 interface state
+  const double hb = 0.5 * (hl + hr);
+  const R hdev = hlR * e0l + hrR * e0r;
+  // h_l E_l - h_r E_r with h E = sqrt(G/(4 pi)) h^{3/2} e^{-lam U^2}: written
+  // through the double difference h_l - h_r so that it vanishes exactly for
+  // equal depths and velocities whatever the rounding or contraction
+  const R xl = r_exp<R>(-laml * Ul * Ul), xr = r_exp<R>(-lamr * Ur * Ur);
+  const R sl = r_sqrt<R>(hlR), sr = r_sqrt<R>(hrR);
+  const R cphi = r_sqrt<R>(g * (R)(0.25 / 3.14159265358979323846));
+  const R dphi = (R)(hl - hr) * (hlR + sl * sr + hrR) / (sl + sr);
+  const R ediff = cphi * (hlR * sl * (xl - xr) + dphi * xr);
+  const R mbn = (hlR * Ul * mul[0] + hrR * Ur * mur[0]) + ediff;
+  const R mbt = hlR * Vl * mul[0] + hrR * Vr * mur[0];
+  const double hbar = hb + (double)hdev;
+  const R hbR = (R)hbar;
+  const R Ub = mbn / hbR, Vb = mbt / hbR;
+  const R lamb = 1 / (g * hbR), thb = (R)0.5 * g * hbR;
+  R mbp[6], mbm[6], t0, t1;
+  half_moments<R>(Ub, lamb, (R)1, mbp, t0, t1);
+  half_moments<R>(Ub, lamb, (R)-1, mbm, t0, t1);
+  Kern<R> kbl = make_kern<R>(hbR, Ub, Vb, lamb, dnl, dtl, Dl);
+  Kern<R> kbr = make_kern<R>(hbR, Ub, Vb, lamb, dnr, dtr, Dr);
+  Kern<R> kl = make_kern<R>(hlR, Ul, Vl, laml, dnl, dtl, Dl);
+  Kern<R> kr = make_kern<R>(hrR, Ur, Vr, lamr, dnr, dtr, Dr);
+  R P[5][6], a[6], b[6];
+  // C2: equilibrium slopes and force, two-sided
+  kern_moments<R>(kbl, mbp, thb, Ub, Vb, a);
+  kern_moments<R>(kbr, mbm, thb, Ub, Vb, b);
+  for (int k = 0; k < 6; k++) P[1][k] = hbR * (a[k] + b[k]);
+  // C3: A-bar from compatibility, d = time derivative of (h, hU, hV)
+  const R dh = -P[1][0], dm = -P[1][1], dn = -P[1][2];
+  P[2][0] = dh; P[2][1] = dm; P[2][2] = dn;
+  P[2][3] = dm;
+  P[2][4] = 2 * Ub * dm - Ub * Ub * dh + 2 * thb * dh;
+  P[2][5] = Vb * dm + Ub * dn - Ub * Vb * dh;
+  // C5: free transport of the initial slopes and force
+  kern_moments<R>(kl, mul, thl, Ul, Vl, a);
+  kern_moments<R>(kr, mur, thr, Ur, Vr, b);
+  for (int k = 0; k < 6; k++) P[4][k] = hlR * a[k] + hrR * b[k];
+  // C1 (full-space moments of g-bar) and C4 (g^l, g^r on their half spaces),
+  // deviations from the bases h_b and G h_b^2 / 2
+  P[0][0] = hdev; P[0][1] = mbn; P[0][2] = mbt;
+  P[0][3] = mbn;
+  P[0][4] = mbn * Ub + g * (R)hb * hdev + (R)0.5 * g * hdev * hdev;
+  P[0][5] = mbn * Vb;
+  P[3][0] = hdev; P[3][1] = mbn; P[3][2] = mbt;
+  P[3][3] = mbn;
+  {
+    const R m2l = thl * e0l - Ul * El, m2r = thr * e0r + Ur * Er;   // mu_2 - th/2 on each side
+    P[3][4] = hlR * (Ul * Ul * mul[0] + 2 * Ul * mul[1] + m2l) + hrR * (Ur * Ur * mur[0] + 2 * Ur * mur[1] + m2r) +
+              (R)(0.125 * G * (hl - hr) * (hl - hr));
+  }
+  P[3][5] = hlR * Vl * (Ul * mul[0] + mul[1]) + hrR * Vr * (Ur * mur[0] + mur[1]);
+  // fitted value and derivative at the stage start
+  R qd[5], qh[5];
+  const R tauR = (R)tau, dR = (R)delta;
+  time_ints<R>(tauR, dR, qd);
+  time_ints<R>(tauR, (R)0.5 * dR, qh);
+  R kv[5], kd[5];
+  const R id = 1 / dR;
+  for (int i = 0; i < 5; i++) {
+    kv[i] = (4 * qh[i] - qd[i]) * id;
+    kd[i] = 4 * (qd[i] - 2 * qh[i]) * id * id;
+  }
+  R f[3] = {0, 0, 0}, ft[3] = {0, 0, 0}, w[3] = {0, 0, 0}, wt[3] = {0, 0, 0};
+  for (int i = 0; i < 5; i++)
+    for (int k = 0; k < 3; k++) {
+      w[k] += kv[i] * P[i][k];
+      wt[k] += kd[i] * P[i][k];
+      f[k] += kv[i] * P[i][3 + k];
+      ft[k] += kd[i] * P[i][3 + k];
+    }
+  W[0] = hb + (double)w[0];
+  W[1] = (double)w[1];
+  W[2] = (double)w[2];
+  F[0] = (double)f[0];
+  F[1] = 0.5 * G * hb * hb + (double)f[1];
+  F[2] = (double)f[2];
+  for (int k = 0; k < 3; k++) { Wt[k] = (double)wt[k]; Ft[k] = (double)ft[k]; }
+}
+
+// ---------------------------------------------------- interface (iface) unit
+// Blended level at one Gauss point of edge e for layer ell (Sec. 2.3):
+// h-hat = xi h^l + (1 - xi) h^r, xi = erfc((U_n^l + U_n^r)/2)/2, with the
+// lower layer blended as the water level eta1 (B is continuous).
+template <typename R>
+__host__ __device__ inline double iface_unit(const Dev &d, int e, int ell, int q) {
+  const int NE = d.ne;
+  const R *xl = (const R *)d.exiL, *xr = (const R *)d.exiR;
+  int cL = d.eL[e], cR = d.eR[e], xf = d.exf[e];
+  double bq = q == 0 ? d.eb0[e] : d.eb1[e];
+  SideVals<R> sl, sr;
+  side_vals<R>(d, ell, cL, 0, xl[(2 * q) * NE + e], xl[(2 * q + 1) * NE + e], bq, sl);
+  side_vals<R>(d, ell, cR, xf, xr[(2 * q) * NE + e], xr[(2 * q + 1) * NE + e], bq, sr);
+  const R n0 = (R)d.en0[e], n1 = (R)d.en1[e];
+  R ul = (sl.mx * n0 + sl.my * n1) / (R)sl.h;
+  R ur = (sr.mx * n0 + sr.my * n1) / (R)sr.h;
+  R xi = (R)0.5 * r_erfc<R>((R)0.5 * (ul + ur));
+  return sr.lev + (double)xi * (sl.lev - sr.lev);
+}
+
+// plane gradient (Sec. 2.3) of the blended level `which` for cell c
+__host__ __device__ __forceinline__ void plane_grad(const Dev &d, int c, int which, double g[2]) {
+  const int N = d.nt, NE = d.ne;
+  g[0] = g[1] = 0;
+  for (int f = 0; f < 3; f++) {
+    int ce = d.cedge[f * N + c];
+    int e = ce >= 0 ? ce : ~ce;
+    double v = d.hc[which * NE + e];
+    g[0] += d.plane[(f * 2) * N + c] * v;
+    g[1] += d.plane[(f * 2 + 1) * N + c] * v;
+  }
+}
+
+// ------------------------------------------------------------- edge unit
+// Interface solution of layer ell at Gauss point q of edge e, global frame:
+// out[0..2] = F, out[3..5] = F_t, out[6..8] = W, out[9..11] = W_t.
+template <typename R>
+__host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int ell, int q, int stage,
+                                          double out[12]) {
+  const int NE = d.ne;
+  const R *xl = (const R *)d.exiL, *xr = (const R *)d.exiR;
+  int cL = d.eL[e], cR = d.eR[e], xf = d.exf[e];
+  const double dt = d.dt[d.inst[cL]];
+  const double delta = stage == 1 ? dt : 0.5 * dt;
+  double bq = q == 0 ? d.eb0[e] : d.eb1[e];
+  SideVals<R> s[2];
+  side_vals<R>(d, ell, cL, 0, xl[(2 * q) * NE + e], xl[(2 * q + 1) * NE + e], bq, s[0]);
+  side_vals<R>(d, ell, cR, xf, xr[(2 * q) * NE + e], xr[(2 * q + 1) * NE + e], bq, s[1]);
+  // blended derivative of the other layer's level and the well-balance vector
+  // D = grad h - grad Phi / G = grad(level) + c (w grad(other) + (1 - w) grad P1)
+  const int oth = 1 - ell;  // hc / omg index of the other layer: 0 = eta1, 1 = h2
+  const R *om = (const R *)d.omg;
+  R w = om[oth * d.nt + cL] < om[oth * d.nt + cR] ? om[oth * d.nt + cL] : om[oth * d.nt + cR];
+  w = w < (R)0 ? (R)0 : (w > (R)1 ? (R)1 : w);
+  double pl0[2], pl1[2];
+  plane_grad(d, cL, oth, pl0);
+  plane_grad(d, cR, oth, pl1);
+  R pl[2][2] = {{(R)pl0[0], (R)pl0[1]}, {(R)pl1[0], (R)pl1[1]}};
+  if (xf != 0) rot2<R>(d.xf + 4 * xf, pl[1]);
+  const R cf = (R)(ell == 0 ? p.chi : 1.0);
+  const R n0 = (R)d.en0[e], n1 = (R)d.en1[e];
+  R U[2], V[2], dn[2][3], dtt[2][3], D[2][2];
+  for (int sd = 0; sd < 2; sd++) {
+    const SideVals<R> &S = s[sd];
+    R Dx = S.glev[0] + cf * (w * S.goth[0] + (1 - w) * pl[sd][0]);
+    R Dy = S.glev[1] + cf * (w * S.goth[1] + (1 - w) * pl[sd][1]);
+    D[sd][0] = Dx * n0 + Dy * n1;
+    D[sd][1] = -Dx * n1 + Dy * n0;
+    R ih = (R)1 / (R)S.h;
+    U[sd] = (S.mx * n0 + S.my * n1) * ih;
+    V[sd] = (-S.mx * n1 + S.my * n0) * ih;
+    // derivatives along n and t of (h, m_n, m_t)
+    const R dir[2][2] = {{n0, n1}, {-n1, n0}};
+    R *outv[2] = {dn[sd], dtt[sd]};
+    for (int k = 0; k < 2; k++) {
+      R ex = dir[k][0], ey = dir[k][1];
+      R dhh = S.gh[0] * ex + S.gh[1] * ey;
+      R dmx = S.gm[0][0] * ex + S.gm[0][1] * ey;
+      R dmy = S.gm[1][0] * ex + S.gm[1][1] * ey;
+      outv[k][0] = dhh;
+      outv[k][1] = dmx * n0 + dmy * n1;
+      outv[k][2] = -dmx * n1 + dmy * n0;
+    }
+  }
+  const double hl = s[0].h, hr = s[1].h;
+  // collision time (Sec. 4): tau = eps dt + eps_num |(hl^2 - hr^2)/(hl^2 + hr^2)| dt
+  const R dlr = (R)(hl - hr), slr = (R)(hl + hr);
+  const R hl2 = (R)hl * (R)hl, hr2 = (R)hr * (R)hr;
+  R jump = dlr * slr / (hl2 + hr2);
+  jump = jump < 0 ? -jump : jump;
+  const double tau = (double)((R)p.eps * (R)dt + (R)p.eps_num * jump * (R)dt);
+  double F[3], Ft[3], W[3], Wt[3];
+  gks_layer<R>(hl, hr, U[0], V[0], U[1], V[1], dn[0], dtt[0], D[0], dn[1], dtt[1], D[1], p.g, tau, delta, F, Ft,
+               W, Wt);
+  const double dn0 = d.en0[e], dn1 = d.en1[e];
+  const double *src[4] = {F, Ft, W, Wt};
+  for (int k = 0; k < 4; k++) {
+    out[3 * k] = src[k][0];
+    out[3 * k + 1] = src[k][1] * dn0 - src[k][2] * dn1;
+    out[3 * k + 2] = src[k][1] * dn1 + src[k][2] * dn0;
+  }
+}
+
+// ------------------------------------------------------------- cell unit
+// Flux and source residuals, S2O4 update (Eq. SWE-fully-discrete), interface
+// values at the stage end (Eq. S2O3) and Gauss-theorem gradients (Eq. slope-1).
+// Returns the CFL ratio dX/U_max of the new state (stage 2) or 0.
+__host__ __device__ inline double update_unit(const Dev &d, const Par &p, int j, int stage, int *flags) {
+  const int N = d.nt, NE = d.ne;
+  const double dt = d.dt[d.inst[j]];
+  if (!(dt > 0)) return 0;
+  const double ia = d.inv_area[j];
+  double LF[NV] = {0}, LFt[NV] = {0}, mW[NV] = {0}, mWt[NV] = {0};
+  double GG[NV][2] = {{0}}, GGt[NV][2] = {{0}}, GGn[NV][2] = {{0}};
+  const double *Wcur = stage == 1 ? d.eWn : d.eW;
+  const double cend = stage == 1 ? 0.5 * dt : dt;
+  for (int f = 0; f < 3; f++) {
+    int ce = d.cedge[f * N + j];
+    double sg = ce >= 0 ? 1.0 : -1.0;
+    int e = ce >= 0 ? ce : ~ce;
+    double sl = sg * d.elen[e] * ia;
+    double nx = d.en0[e], ny = d.en1[e];
+    for (int v = 0; v < NV; v++) {
+      double F = d.eF[v * NE + e], Ft = d.eFt[v * NE + e];
+      double W = Wcur[v * NE + e], Wt = d.eWt[v * NE + e], Wn = d.eWn[v * NE + e];
+      LF[v] -= sl * F;
+      LFt[v] -= sl * Ft;
+      mW[v] += W * (1.0 / 3.0);
+      mWt[v] += Wt * (1.0 / 3.0);
+      GG[v][0] += sl * nx * W; GG[v][1] += sl * ny * W;
+      GGt[v][0] += sl * nx * Wt; GGt[v][1] += sl * ny * Wt;
+      double We = Wn + cend * Wt;
+      GGn[v][0] += sl * nx * We; GGn[v][1] += sl * ny * We;
+    }
+  }
+  const double G = p.g;
+  const double gb[2] = {d.bgx[j], d.bgy[j]};
+  double L[NV], Lt[NV], a[NV];
+  for (int v = 0; v < NV; v++) { L[v] = LF[v]; Lt[v] = LFt[v]; a[v] = d.avg[v * N + j]; }
+  for (int l = 0; l < 2; l++) {
+    int b = 3 * l;
+    for (int k = 0; k < 2; k++) {
+      L[b + 1 + k] -= G * a[b] * gb[k];
+      Lt[b + 1 + k] -= G * LF[b] * gb[k];
+    }
+  }
+  for (int k = 0; k < 2; k++) {
+    L[1 + k] -= G * mW[0] * GG[3][k];
+    Lt[1 + k] -= G * (mWt[0] * GG[3][k] + mW[0] * GGt[3][k]);
+    L[4 + k] -= p.chi * G * mW[3] * GG[0][k];
+    Lt[4 + k] -= p.chi * G * (mWt[3] * GG[0][k] + mW[3] * GGt[0][k]);
+  }
+  double nw[NV];
+  for (int v = 0; v < NV; v++) {
+    if (stage == 1) {
+      d.Wn[v * N + j] = a[v];
+      d.Ln[v * N + j] = L[v];
+      d.Ltn[v * N + j] = Lt[v];
+      nw[v] = a[v] + 0.5 * dt * L[v] + 0.125 * dt * dt * Lt[v];
+    } else {
+      nw[v] = d.Wn[v * N + j] + dt * d.Ln[v * N + j] + dt * dt * (1.0 / 6.0) * d.Ltn[v * N + j] +
+              dt * dt * (1.0 / 3.0) * Lt[v];
+    }
+  }
+  for (int v = 0; v < NV; v++) {
+    d.avg[v * N + j] = nw[v];
+    d.grad[(2 * v) * N + j] = GGn[v][0];
+    d.grad[(2 * v + 1) * N + j] = GGn[v][1];
+  }
+  int fl = 0;
+  for (int v = 0; v < NV; v++)
+    if (!isfinite(nw[v]) || !isfinite(GGn[v][0]) || !isfinite(GGn[v][1])) fl |= 2;
+  if (!(nw[0] > 0) || !(nw[3] > 0)) fl |= 1;
+  *flags = fl;
+  if (stage != 2) return 0;
+  double um = 0;
+  for (int l = 0; l < 2; l++) {
+    double h = nw[3 * l], u = nw[3 * l + 1] / h, v = nw[3 * l + 2] / h;
+    double sp = sqrt(u * u + v * v) + sqrt(G * h);
+    um = sp > um ? sp : um;
+  }
+  return d.dX[j] / um;
+}
+
+}  // namespace gks2l
