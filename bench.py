@@ -38,16 +38,42 @@ METRIC = "triangle-stage updates/s vs plain FP64 GPU at stated L1 error; % roofl
 UNIT = "triangle-stage updates/s"
 N_SQ = 1024
 
-# Per-unit work of the kernels, FLOPs counted by the hardware counters
-# (sm__sass_thread_inst_executed_op_{f,d}{add,mul,fma}, FMA = 2) on a
-# 131,072-triangle case, divided by the units of one launch. Units: recon and
-# update per cell, iface and edge per edge.
-FLOPS_PER_UNIT = {
-    "fp32": {"recon": None, "iface": None, "edge": None, "update": None},
-    "fp64": {"recon": None, "iface": None, "edge": None, "update": None},
+# Per-unit work of each kernel: (FP32 flops, FP64 flops, algorithmic DRAM
+# bytes). Flops are the hardware counts (sm__sass_thread_inst_executed_op_
+# {f,d}{add,mul,fma}[2] with FMA = 2 flops) of one launch on a 131,072-cell /
+# 197,120-edge case divided by its units; bytes are the minimum one launch must
+# move with the structure-of-arrays layout (each cell or edge record read or
+# written once). Units: cells for recon and update, edges for iface and edge.
+WORK_PER_UNIT = {
+    "fp32": {"recon": (3830, 236, 1417), "iface": (878, 56, 277), "edge": (6646, 436, 514),
+             "update": (0, 343, 850)},
+    "fp64": {"recon": (69, 4593, 2209), "iface": (15, 1349, 473), "edge": (107, 9162, 696),
+             "update": (0, 343, 850)},
 }
 # Measured FMA-chain peaks of this GB300 pool (TFLOP/s, 2 flops per FMA).
-PEAK_TFLOPS = {"fp32": None, "fp64": None}
+PEAK_TFLOPS = {"fp32": 76.5, "fp64": 1.254}
+# DRAM bytes per unit (dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch on the 131,072-cell case, per unit; traffic grows with the units).
+TRAFFIC_PER_UNIT = {"fp32": {"recon": 1318.0, "iface": 277.0, "edge": 416.0, "update": 431.0}}
+
+
+def roofline(form, kernel, units, ms, hbm_gbs):
+    """Binding limit of one kernel launch: the slowest of its FP32 work at the
+    FP32 peak, its FP64 work at the FP64 peak and its algorithmic bytes at the
+    measured HBM bandwidth; achieved is that resource's rate in this launch."""
+    f32, f64, by = WORK_PER_UNIT[form][kernel]
+    t = ms * 1e-3
+    limits = {"fp32": f32 * units / (PEAK_TFLOPS["fp32"] * 1e12),
+              "fp64": f64 * units / (PEAK_TFLOPS["fp64"] * 1e12),
+              "hbm": by * units / (hbm_gbs * 1e9)}
+    bind = max(limits, key=limits.get)
+    if bind == "hbm":
+        return {"bound": "hbm", "kernel": "k_" + kernel, "achieved": by * units / t / 1e9, "peak": hbm_gbs,
+                "unit": "GB/s", "frac": limits[bind] / t, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    work = f32 if bind == "fp32" else f64
+    return {"bound": "alu", "pipe": bind, "kernel": "k_" + kernel, "achieved": work * units / t / 1e12,
+            "peak": PEAK_TFLOPS[bind], "unit": "TFLOP/s", "frac": limits[bind] / t,
+            "peak_source": "measured %s FMA-chain peak on this pool" % bind.upper()}
 
 
 def read_peaks():
@@ -204,6 +230,7 @@ def main():
 
     prob = inputs.lake_at_rest(args.n, chi=0.98)
     nt = prob.mesh.n_tri
+    n_edges = (3 * nt + 2 * (prob.mesh.nx + prob.mesh.ny)) // 2
     stream = torch.cuda.Stream(device=dev)
     results = {}
     for form, prec in (("fp32", g.GKS2L_FP32), ("fp64", g.GKS2L_FP64)):
@@ -254,8 +281,9 @@ def main():
             del s
             torch.cuda.empty_cache()
 
-    area = np.abs(0.5 * np.cross(prob.mesh.xy[prob.mesh.tri[:, 1]] - prob.mesh.xy[prob.mesh.tri[:, 0]],
-                                 prob.mesh.xy[prob.mesh.tri[:, 2]] - prob.mesh.xy[prob.mesh.tri[:, 0]]))
+    P = prob.mesh.xy[prob.mesh.tri]
+    area = 0.5 * np.abs((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1]) -
+                        (P[:, 1, 1] - P[:, 0, 1]) * (P[:, 2, 0] - P[:, 0, 0]))
     l1 = max(float(np.sum(area * np.abs(results["fp32"]["state"][v] - results["fp64"]["state"][v])) /
                    np.sum(area * np.abs(results["fp64"]["state"][v]))) for v in (0, 3))
 
@@ -265,19 +293,16 @@ def main():
     # roofline of the dominant kernel of the headline form
     kern = r32["kernels"]
     top = max(("recon", "iface", "edge", "update"), key=lambda k: kern[k])
-    units = nt if top in ("recon", "update") else int(round(1.5 * nt))
-    fpu = FLOPS_PER_UNIT["fp32"][top]
-    peak = PEAK_TFLOPS["fp32"]
-    roof = {"bound": "alu", "kernel": "k_" + top, "unit": "TFLOP/s", "traffic": None}
-    if fpu and peak:
-        achieved = fpu * units / (kern[top] * 1e-3) / 1e12
-        roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
-                     "peak_source": "measured FP32 FMA-chain peak on this pool"})
-    else:
-        roof.update({"achieved": None, "peak": None, "frac": None})
+    units = nt if top in ("recon", "update") else n_edges
+    hbm = read_peaks().get("hbm_gbs", 6800.0)
+    roof = roofline("fp32", top, units, kern[top], hbm)
+    tpu = TRAFFIC_PER_UNIT.get("fp32", {}).get(top)
+    roof["traffic"] = tpu * units if tpu else None
+    roof["per_kernel"] = {k: round(roofline("fp32", k, nt if k in ("recon", "update") else n_edges, kern[k],
+                                             hbm)["frac"], 4) for k in ("recon", "iface", "edge", "update")}
     share = {k: kern[k] / sum(kern[x] for x in ("recon", "iface", "edge", "update")) for k in
              ("recon", "iface", "edge", "update")}
-    launches = steps_launch = 1 + 2 * 4
+    launches_per_step = 1 + 2 * 4   # step start + 4 kernels per stage
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": r32["steps"],
         "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -297,7 +322,7 @@ def main():
         "roofline": roof,
         "clocks": r32["clocks"],
         "e2e": r32["e2e"],
-        "gpu_launches": launches * r32["steps"],
+        "gpu_launches": launches_per_step * r32["steps"],
         "cpu_baseline": cpu,
     }
     if rank == 0:
