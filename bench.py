@@ -73,7 +73,7 @@ def roofline(form, kernel, units, ms, hbm_gbs):
     work = f32 if bind == "fp32" else f64
     return {"bound": "alu", "pipe": bind, "kernel": "k_" + kernel, "achieved": work * units / t / 1e12,
             "peak": PEAK_TFLOPS[bind], "unit": "TFLOP/s", "frac": limits[bind] / t,
-            "peak_source": "measured %s FMA-chain peak on this pool" % bind.upper()}
+            "peak_source": "measured %s FMA-chain peak (gks2l_alu_peaks, same run)" % bind.upper()}
 
 
 def read_peaks():
@@ -85,7 +85,7 @@ def read_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    """nvidia-smi clock/throttle samples every 50 ms while a region runs."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -94,40 +94,46 @@ class ClockSampler:
     def __init__(self, index=0):
         self.index = index
         self.samples = []
-        self._stop = threading.Event()
-        self._t = None
-
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+        self._p = None
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        try:
+            self._p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                        "--format=csv,noheader,nounits", "-lms", "50"],
+                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)   # let the first sample land before the timed region
+        except OSError:
+            self._p = None
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
-        self._t.join(timeout=10)
+        if self._p is None:
+            return
+        time.sleep(0.1)
+        self._p.terminate()
+        try:
+            out, _ = self._p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self._p.kill()
+            out, _ = self._p.communicate()
+        self.samples = [[x.strip() for x in line.split(",")] for line in out.splitlines() if line.strip()]
 
     def summary(self):
-        if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
-        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        rows = [r for r in self.samples if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[1]) for r in rows) if v is not None]
+        mx = [v for v in (num(r[2]) for r in rows) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 5 + i and "Active" in s[5 + i]
-                          and "Not" not in s[5 + i]})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 def dist_env():
@@ -189,17 +195,35 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_profile_case(args):
+    from paper_2306_04467_gb300 import gks2l as g
+    from paper_2306_04467_gb300 import inputs
+    prob = inputs.lake_at_rest(args.profile_case, chi=0.98)
+    prec = g.GKS2L_FP32 if args.form == "fp32" else g.GKS2L_FP64
+    par = g.default_params(g=prob.g, chi=prob.chi, cfl=prob.cfl, precision=prec)
+    s = g.Solver(prob.mesh, par, prob.b_vert)
+    s.set_state(prob.avg, prob.grad)
+    print(json.dumps({"profile_case": args.profile_case, "form": args.form, "n_tri": prob.mesh.n_tri,
+                      "kernel_ms": s.profile_kernels(1)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_SQ, help="squares per side of the mesh")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", type=int, default=0,
+                    help="profiling mode: one step of the workload at this many squares per side, kernels "
+                         "launched one by one (for ncu captures of a small case)")
+    ap.add_argument("--form", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args)
 
     import torch
     ws, rank, local = dist_env()
@@ -233,6 +257,7 @@ def main():
     n_edges = (3 * nt + 2 * (prob.mesh.nx + prob.mesh.ny)) // 2
     stream = torch.cuda.Stream(device=dev)
     results = {}
+    live_peaks = None
     for form, prec in (("fp32", g.GKS2L_FP32), ("fp64", g.GKS2L_FP64)):
         with torch.cuda.stream(stream):
             par = g.default_params(g=prob.g, chi=prob.chi, cfl=prob.cfl, precision=prec)
@@ -259,6 +284,8 @@ def main():
                 raise RuntimeError("device status %d after the timed run" % st["status"])
             a, _ = s.get_state()
             kern = s.profile_kernels(2)
+            if form == "fp32":
+                live_peaks = s.alu_peaks()
             results[form] = {"ms_per_step": ms, "steps": steps, "clocks": sampler.summary(), "kernels": kern,
                              "state": a, "workspace": s.workspace_bytes}
             # end to end through the C ABI with host (pinned) buffers
@@ -295,6 +322,8 @@ def main():
     top = max(("recon", "iface", "edge", "update"), key=lambda k: kern[k])
     units = nt if top in ("recon", "update") else n_edges
     hbm = read_peaks().get("hbm_gbs", 6800.0)
+    if live_peaks:
+        PEAK_TFLOPS.update(live_peaks)
     roof = roofline("fp32", top, units, kern[top], hbm)
     tpu = TRAFFIC_PER_UNIT.get("fp32", {}).get(top)
     roof["traffic"] = tpu * units if tpu else None
@@ -320,6 +349,7 @@ def main():
         "kernel_ms": {k: round(v, 4) for k, v in kern.items()},
         "kernel_share": {k: round(v, 4) for k, v in share.items()},
         "roofline": roof,
+        "alu_peaks_tflops": live_peaks,
         "clocks": r32["clocks"],
         "e2e": r32["e2e"],
         "gpu_launches": launches_per_step * r32["steps"],

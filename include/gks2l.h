@@ -176,6 +176,12 @@ int gks2l_harvest(gks2l_ctx *ctx, float tol, float *d_features, float *d_labels)
  * stages), step start. Requires a state and phase at a step boundary. */
 int gks2l_profile_kernels(gks2l_ctx *ctx, int32_t n_steps, double ms[5]);
 
+/* Measurement helper with no counterpart in the paper: FP32 and FP64 FMA
+ * throughput of the bound device (TFLOP/s, FMA = 2 flops) from FMA-chain
+ * kernels on the bound stream, the denominators of the ALU rooflines.
+ * Uses the context's staging area (needs n_tri >= 8 * SMs * 256 / 18). */
+int gks2l_alu_peaks(gks2l_ctx *ctx, double tflops[2]);
+
 /* Human-readable name of a status code. */
 const char *gks2l_error_string(int code);
 

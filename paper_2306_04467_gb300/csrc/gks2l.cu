@@ -202,6 +202,22 @@ __global__ void k_scatter(int nt, int nvar, const int *perm, const double *src, 
   for (int v = 0; v < nvar; v++) dst[(size_t)v * nt + c] = src[(size_t)v * nt + j];
 }
 
+// FMA-chain throughput probe for the roofline denominators (measurement only)
+template <typename T>
+__global__ void k_fma_probe(T *out, int iters, T a, T b) {
+  T acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) acc[i] = (T)(threadIdx.x + i);
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) acc[i] = acc[i] * a + b;
+  }
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; i++) s += acc[i];
+  if (s == (T)-1.2345) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // ------------------------------------------------------------- workspace
 struct Carver {
   char *base;
@@ -682,6 +698,40 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[5]) {
   for (int k = 0; k < 4; k++) ms[k] = acc[k] / (2.0 * n_steps);
   ms[4] = acc[4] / n_steps;
   c->stages += 2 * n_steps;
+  return GKS2L_OK;
+}
+
+int gks2l_alu_peaks(gks2l_ctx *c, double tflops[2]) {
+  if (!c || !tflops) return GKS2L_EINVAL;
+  if (!c->bound) return GKS2L_ESTATE;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int nb = sms * 8, nth = 256;
+  // the stores are never taken (the sums cannot equal the sentinel); the
+  // staging area is large enough for every thread all the same
+  if ((size_t)nb * nth > 18 * (size_t)c->prep.nt) return GKS2L_ESPACE;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int it32 = 20000, it64 = 2000;
+  for (int rep = 0; rep < 2; rep++) {
+    float ms32 = 0, ms64 = 0;
+    CK(cudaEventRecord(e0, c->stream));
+    k_fma_probe<float><<<nb, nth, 0, c->stream>>>((float *)c->d_stage, it32, 0.999f, 0.001f);
+    CK(cudaEventRecord(e1, c->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&ms32, e0, e1));
+    CK(cudaEventRecord(e0, c->stream));
+    k_fma_probe<double><<<nb, nth, 0, c->stream>>>(c->d_stage, it64, 0.999, 0.001);
+    CK(cudaEventRecord(e1, c->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&ms64, e0, e1));
+    tflops[0] = 16.0 * it32 * (double)nb * nth / (ms32 * 1e-3) / 1e12;
+    tflops[1] = 16.0 * it64 * (double)nb * nth / (ms64 * 1e-3) / 1e12;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   return GKS2L_OK;
 }
 

@@ -60,6 +60,7 @@ SIGNATURES = {
     "gks2l_get_state_device": (_I, [_P, _P, _P]),
     "gks2l_stats": (_I, [_P, ctypes.POINTER(gks2l_stats_t)]),
     "gks2l_profile_kernels": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double * 5)]),
+    "gks2l_alu_peaks": (_I, [_P, ctypes.POINTER(ctypes.c_double * 2)]),
     "gks2l_set_mlp": (_I, [_P, _P, ctypes.c_size_t]),
     "gks2l_harvest": (_I, [_P, ctypes.c_float, _P, _P]),
     "gks2l_error_string": (ctypes.c_char_p, [_I]),
@@ -211,6 +212,12 @@ class Solver:
         ms = (ctypes.c_double * 5)()
         _check(load().gks2l_profile_kernels(self._h, int(n_steps), ctypes.byref(ms)), "gks2l_profile_kernels")
         return {"recon": ms[0], "iface": ms[1], "edge": ms[2], "update": ms[3], "step_begin": ms[4]}
+
+    def alu_peaks(self):
+        """Measured FP32 and FP64 FMA throughput of the device, TFLOP/s."""
+        t = (ctypes.c_double * 2)()
+        _check(load().gks2l_alu_peaks(self._h, ctypes.byref(t)), "gks2l_alu_peaks")
+        return {"fp32": t[0], "fp64": t[1]}
 
     def set_mlp(self, params_f32: np.ndarray):
         p = np.ascontiguousarray(params_f32, dtype=np.float32)
