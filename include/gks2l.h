@@ -44,6 +44,7 @@ extern "C" {
 #define GKS2L_ENONFINITE -6  /* a non-finite value appeared on the device           */
 #define GKS2L_ESPACE -7      /* workspace too small                                 */
 #define GKS2L_ENOTIMPL -8
+#define GKS2L_ETOOBIG -9     /* size beyond a fixed maximum (gks2l_cfl_mass_noalloc) */
 
 /* boundary kinds per triangle edge (edge k runs from tri[k] to tri[(k+1)%3]) */
 #define GKS2L_BC_INTERIOR 0
@@ -181,6 +182,33 @@ int gks2l_profile_kernels(gks2l_ctx *ctx, int32_t n_steps, double ms[5]);
  * kernels on the bound stream, the denominators of the ALU rooflines.
  * Uses the context's staging area (needs n_tri >= 8 * SMs * 256 / 18). */
 int gks2l_alu_peaks(gks2l_ctx *ctx, double tflops[2]);
+
+/* CFL step and layer masses of a device state, allocating nothing.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * call cudaMalloc -- code running inside another framework's memory pool, a
+ * process whose device memory is fully reserved up front, or a loop that must
+ * not allocate -- and so cannot provide the workspace gks2l_bind needs. It
+ * computes what the library's own CFL kernel computes for a bound context
+ * (Sec. 4: dt = CFL * min_j dX_j / U_max,j, U_max = max over layers of
+ * |U| + sqrt(G h); plus sum_j |Omega_j| h_j per layer), with its scratch in a
+ * fixed device array of 3 x 1024 doubles (24 KB) that every GPU loading the
+ * library holds until the process exits.
+ *   n_tri   number of cells, 1 .. GKS2L_NOALLOC_MAX_TRI (larger: GKS2L_ETOOBIG)
+ *   d_avg   device, 6*n_tri doubles, variable-major state (any cell order)
+ *   d_area  device, n_tri cell areas, d_dX device, n_tri CFL lengths
+ *           (4 |Omega| / perimeter), both in the same cell order as d_avg
+ *   d_out   device, 3 doubles written: dt, mass of layer 1 (lower), mass of
+ *           layer 2
+ *   stream  cudaStream_t (NULL = default stream); the call only enqueues work.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls share the one array, so calls whose
+ * work overlaps on the GPU (other streams, other threads) race; serialise
+ * them. Nothing in the array needs clearing: each call overwrites the slots it
+ * reads. Calls no cudaMalloc, cudaFree or allocating library routine. */
+#define GKS2L_NOALLOC_MAX_TRI (1 << 28)
+int gks2l_cfl_mass_noalloc(int32_t n_tri, const double *d_avg, const double *d_area, const double *d_dX,
+                           double g, double cfl, double *d_out, void *stream);
 
 /* Human-readable name of a status code. */
 const char *gks2l_error_string(int code);

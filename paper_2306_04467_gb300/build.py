@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gks2l.cu", "prep.cpp", "mlp.cu"]
+SOURCES = ["gks2l.cu", "prep.cpp", "noalloc.cu", "mlp.cu"]
 
 
 def _stale(target, deps):

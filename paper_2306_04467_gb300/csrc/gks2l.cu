@@ -756,6 +756,7 @@ const char *gks2l_error_string(int code) {
     case GKS2L_ENONFINITE: return "non-finite value";
     case GKS2L_ESPACE: return "workspace too small";
     case GKS2L_ENOTIMPL: return "not implemented";
+    case GKS2L_ETOOBIG: return "size beyond the fixed maximum of this entry point";
     default: return "unknown status";
   }
 }

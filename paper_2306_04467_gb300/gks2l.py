@@ -63,6 +63,7 @@ SIGNATURES = {
     "gks2l_alu_peaks": (_I, [_P, ctypes.POINTER(ctypes.c_double * 2)]),
     "gks2l_set_mlp": (_I, [_P, _P, ctypes.c_size_t]),
     "gks2l_harvest": (_I, [_P, ctypes.c_float, _P, _P]),
+    "gks2l_cfl_mass_noalloc": (_I, [ctypes.c_int32, _P, _P, _P, _D, _D, _P, _P]),
     "gks2l_error_string": (ctypes.c_char_p, [_I]),
     "gks2l_destroy": (None, [_P]),
 }
@@ -237,6 +238,15 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def cfl_mass_noalloc(avg, area, dX, g, cfl, out, stream=None):
+    """gks2l_cfl_mass_noalloc on device tensors (float64, same cell order):
+    writes (dt, mass of layer 1, mass of layer 2) into `out` (3 doubles)."""
+    n = area.numel()
+    s = _P(stream.cuda_stream) if stream is not None else None
+    _check(load().gks2l_cfl_mass_noalloc(n, _P(avg.data_ptr()), _P(area.data_ptr()), _P(dX.data_ptr()),
+                                         float(g), float(cfl), _P(out.data_ptr()), s), "gks2l_cfl_mass_noalloc")
 
 
 def problem_solver(prob, precision=GKS2L_FP64, **kw):

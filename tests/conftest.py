@@ -11,3 +11,12 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long CPU test")
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built_library():
+    """Compile (or reuse) the CUDA library and the oracle before any test."""
+    from paper_2306_04467_gb300 import build as B
+    B.build()
+    from oracle import oracle
+    oracle.build()
