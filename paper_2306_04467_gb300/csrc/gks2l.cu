@@ -45,9 +45,9 @@ __global__ void __launch_bounds__(128) k_iface(Dev d) {
   bool ok = e < d.ne;
   int ee = ok ? e : d.ne - 1;
   ok = ok && d.dt[d.inst[d.eL[ee]]] > 0;
-  double v = ok ? iface_unit<R>(d, ee, ell, q) : 0.0;
-  double s = v + __shfl_xor_sync(FULL, v, 1);
-  if (ok && q == 0) d.hc[ell * d.ne + e] = 0.5 * s;
+  R v = ok ? iface_unit<R>(d, ee, ell, q) : (R)0;
+  R s = v + __shfl_xor_sync(FULL, v, 1);
+  if (ok && q == 0) ((R *)d.hc)[ell * d.ne + e] = (R)0.5 * s;
 }
 
 template <typename R>
@@ -57,27 +57,27 @@ __global__ void __launch_bounds__(128) k_edge(Dev d, Par p, int stage) {
   bool ok = e < d.ne;
   int ee = ok ? e : d.ne - 1;
   ok = ok && d.dt[d.inst[d.eL[ee]]] > 0;
-  double out[12];
+  R out[12];
   if (ok) {
     edge_unit<R>(d, p, ee, ell, q, stage, out);
   } else {
     for (int k = 0; k < 12; k++) out[k] = 0;
   }
 #pragma unroll
-  for (int k = 0; k < 12; k++) out[k] = 0.5 * (out[k] + __shfl_xor_sync(FULL, out[k], 1));
+  for (int k = 0; k < 12; k++) out[k] = (R)0.5 * (out[k] + __shfl_xor_sync(FULL, out[k], 1));
   if (!ok) return;
   const int NE = d.ne;
   const int vb = ell == 0 ? 3 : 0;
   if (q == 0) {
     for (int k = 0; k < 3; k++) {
-      d.eF[(vb + k) * NE + e] = out[k];
-      d.eFt[(vb + k) * NE + e] = out[3 + k];
+      ((R *)d.eF)[(vb + k) * NE + e] = out[k];
+      ((R *)d.eFt)[(vb + k) * NE + e] = out[3 + k];
     }
   } else {
-    double *Wd = stage == 1 ? d.eWn : d.eW;
+    R *Wd = (R *)(stage == 1 ? d.eWn : d.eW);
     for (int k = 0; k < 3; k++) {
       Wd[(vb + k) * NE + e] = out[6 + k];
-      d.eWt[(vb + k) * NE + e] = out[9 + k];
+      ((R *)d.eWt)[(vb + k) * NE + e] = out[9 + k];
     }
   }
 }
@@ -113,6 +113,7 @@ __device__ __forceinline__ void reduce_cell_stats(const Dev &d, bool ok, int ins
   }
 }
 
+template <typename R>
 __global__ void __launch_bounds__(128) k_update(Dev d, Par p, int stage) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   bool ok = j < d.nt;
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(128) k_update(Dev d, Par p, int stage) {
   double ratio = INFINITY;
   int fl = 0;
   if (ok) {
-    double r = update_unit(d, p, j, stage, &fl);
+    double r = update_unit<R>(d, p, j, stage, &fl);
     if (r > 0) ratio = r;
   }
   if (fl) atomicOr(d.status, fl);
@@ -188,6 +189,51 @@ __global__ void k_step_begin(Dev d, Par p, const double *tend) {
   d.mass[2 * i] = d.mass[2 * i + 1] = 0;
 }
 
+// deviation mirrors of a freshly set state: dq, dg (gradients given in the
+// caller's order, grad h1 -> grad eta1 = grad h1 + grad B), R1 - B per cell
+template <typename R>
+__global__ void k_mirrors(Dev d, const int *perm, const double *grad_caller) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.nt) return;
+  const int N = d.nt, in = d.inst[j], c = perm[j];
+  R *dq = (R *)d.dq, *dg = (R *)d.dg;
+  const double R2 = d.ref[2 * in], R1 = d.ref[2 * in + 1];
+  dq[j] = (R)(d.avg[j] - R2);
+  dq[3 * N + j] = (R)((d.avg[3 * N + j] + d.bmean[j]) - R1);
+  for (int v : {1, 2, 4, 5}) dq[v * N + j] = (R)d.avg[v * N + j];
+  for (int k = 0; k < 12; k++) {
+    double gk = grad_caller ? grad_caller[(size_t)k * N + c] : 0.0;
+    if (k == 6) gk += d.bgx[j];
+    if (k == 7) gk += d.bgy[j];
+    dg[k * N + j] = (R)gk;
+  }
+  ((R *)d.hrefc)[j] = (R)(R1 - d.bmean[j]);
+}
+
+template <typename R>
+__global__ void k_edge_ref(Dev d) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.ne) return;
+  const double R1 = d.ref[2 * d.inst[d.eL[e]] + 1];
+  ((R *)d.hrefe)[e] = (R)(R1 - d.eb0[e]);
+  ((R *)d.hrefe)[d.ne + e] = (R)(R1 - d.eb1[e]);
+}
+
+// gradients in the caller's order, grad eta1 -> grad h1
+template <typename R>
+__global__ void k_grad_out(Dev d, const int *perm, double *out) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.nt) return;
+  const int N = d.nt, c = perm[j];
+  const R *dg = (const R *)d.dg;
+  for (int k = 0; k < 12; k++) {
+    double gk = (double)dg[k * N + j];
+    if (k == 6) gk -= d.bgx[j];
+    if (k == 7) gk -= d.bgy[j];
+    out[(size_t)k * N + c] = gk;
+  }
+}
+
 // caller order <-> device order
 __global__ void k_gather(int nt, int nvar, const int *perm, const double *src, double *dst) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -245,6 +291,7 @@ struct gks2l_ctx {
   int *d_perm = nullptr;
   double *d_tend = nullptr;
   double *d_stage = nullptr;   // 18 * nt staging for permutations
+  std::vector<double> bmean_h; // cell-average bottom (device order), host copy
   int phase = 0;
   int64_t stages = 0;
   cudaGraph_t graph = nullptr;
@@ -261,7 +308,6 @@ size_t layout(gks2l_ctx *c, char *base) {
   Dev &d = c->d;
   d.nt = P.nt; d.ne = P.ne; d.ninst = P.ninst;
   d.inst = k.take<int>(nt);
-  d.inv_area = k.take<double>(nt);
   d.area = k.take<double>(nt);
   d.hs = k.take<double>(nt);
   d.dX = k.take<double>(nt);
@@ -274,11 +320,14 @@ size_t layout(gks2l_ctx *c, char *base) {
   d.p1op = k.take<char>(rs * 30 * nt);
   d.bq = k.take<char>(rs * kBeta * nt);
   d.mmean = k.take<char>(rs * 7 * nt);
-  d.plane = k.take<double>(6 * nt);
+  d.plane = k.take<char>(rs * 6 * nt);
   d.cedge = k.take<int>(3 * nt);
+  d.fsl = k.take<double>(3 * nt);
   d.inst_first = k.take<int>(ni + 1);
   d.avg = k.take<double>(6 * nt);
-  d.grad = k.take<double>(12 * nt);
+  d.dq = k.take<char>(rs * 6 * nt);
+  d.dg = k.take<char>(rs * 12 * nt);
+  d.hrefc = k.take<char>(rs * nt);
   d.Wn = k.take<double>(6 * nt);
   d.Ln = k.take<double>(6 * nt);
   d.Ltn = k.take<double>(6 * nt);
@@ -288,19 +337,19 @@ size_t layout(gks2l_ctx *c, char *base) {
   d.eL = k.take<int>(ne);
   d.eR = k.take<int>(ne);
   d.exf = k.take<int8_t>(ne);
-  d.en0 = k.take<double>(ne);
-  d.en1 = k.take<double>(ne);
-  d.elen = k.take<double>(ne);
+  d.en = k.take<char>(rs * 2 * ne);
   d.eb0 = k.take<double>(ne);
   d.eb1 = k.take<double>(ne);
   d.exiL = k.take<char>(rs * 4 * ne);
   d.exiR = k.take<char>(rs * 4 * ne);
-  d.hc = k.take<double>(2 * ne);
-  d.eF = k.take<double>(6 * ne);
-  d.eFt = k.take<double>(6 * ne);
-  d.eW = k.take<double>(6 * ne);
-  d.eWt = k.take<double>(6 * ne);
-  d.eWn = k.take<double>(6 * ne);
+  d.hrefe = k.take<char>(rs * 2 * ne);
+  d.hc = k.take<char>(rs * 2 * ne);
+  d.eF = k.take<char>(rs * 6 * ne);
+  d.eFt = k.take<char>(rs * 6 * ne);
+  d.eW = k.take<char>(rs * 6 * ne);
+  d.eWt = k.take<char>(rs * 6 * ne);
+  d.eWn = k.take<char>(rs * 6 * ne);
+  d.ref = k.take<double>(2 * ni);
   d.dt = k.take<double>(ni);
   d.t = k.take<double>(ni);
   d.dtbits = k.take<unsigned long long>(ni);
@@ -338,6 +387,7 @@ int upload_r(gks2l_ctx *c, const void *dst, const std::vector<double> &src, std:
 int upload_bathymetry(gks2l_ctx *c) {
   std::vector<double> bm, bx, by, e0, e1;
   bathymetry(c->prep, c->has_b ? c->bvert.data() : nullptr, bm, bx, by, e0, e1);
+  c->bmean_h = bm;
   int rc;
   if ((rc = upload(c, c->d.bmean, bm)) || (rc = upload(c, c->d.bgx, bx)) || (rc = upload(c, c->d.bgy, by)) ||
       (rc = upload(c, c->d.eb0, e0)) || (rc = upload(c, c->d.eb1, e1)))
@@ -351,7 +401,6 @@ Par make_par(const gks2l_ctx *c) {
   p.g = c->par.g; p.chi = c->par.chi; p.cfl = c->par.cfl;
   p.eps = c->par.eps; p.eps_num = c->par.eps_num;
   p.gam_hi = c->par.weno_gamma_hi; p.weno_eps = c->par.weno_eps;
-  p.t_end = 0;
   p.use_gate = c->par.indicator == GKS2L_INDICATOR_MLP ? 1 : 0;
   return p;
 }
@@ -365,7 +414,7 @@ void launch_stage(gks2l_ctx *c, int stage) {
   k_recon<R><<<blocks(d.nt, 32), dim3(32, 6), 0, c->stream>>>(d, p);
   k_iface<R><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d);
   k_edge<R><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d, p, stage);
-  k_update<<<blocks(d.nt, 128), 128, 0, c->stream>>>(d, p, stage);
+  k_update<R><<<blocks(d.nt, 128), 128, 0, c->stream>>>(d, p, stage);
 }
 
 void launch_stage_any(gks2l_ctx *c, int stage) {
@@ -410,13 +459,50 @@ int check_status(gks2l_ctx *c) {
   return 0;
 }
 
-int after_state(gks2l_ctx *c) {
+// Reference levels per instance: area-weighted means of h2 and eta1 = h1 + B
+// of the state in device order (host, deterministic), rounded to 2^-32.
+int set_references(gks2l_ctx *c, const double *avg_dev_order_host) {
+  const Prep &P = c->prep;
+  const size_t N = P.nt;
+  std::vector<double> ref(2 * P.ninst);
+  for (int i = 0; i < P.ninst; i++) {
+    double a = 0, s2 = 0, s1 = 0;
+    for (int j = P.inst_first[i]; j < P.inst_first[i + 1]; j++) {
+      a += P.area[j];
+      s2 += P.area[j] * avg_dev_order_host[j];
+      s1 += P.area[j] * (avg_dev_order_host[3 * N + j] + c->bmean_h[j]);
+    }
+    ref[2 * i] = std::ldexp(std::nearbyint(std::ldexp(s2 / a, 32)), -32);
+    ref[2 * i + 1] = std::ldexp(std::nearbyint(std::ldexp(s1 / a, 32)), -32);
+  }
+  CK(cudaMemcpyAsync(c->d.ref, ref.data(), ref.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return 0;
+}
+
+// after d.avg (device order) is set and the caller's gradients sit at
+// grad_caller (device memory, caller order, or NULL): references, mirrors,
+// reference depths on the edges, counters, CFL ratio and masses
+int after_state(gks2l_ctx *c, const double *grad_caller) {
+  const size_t N = c->prep.nt;
+  std::vector<double> avg(6 * N);
+  CK(cudaMemcpyAsync(avg.data(), c->d.avg, 6 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  int rc = set_references(c, avg.data());
+  if (rc) return rc;
   Par p = make_par(c);
+  if (c->par.precision == GKS2L_FP32) {
+    k_mirrors<float><<<blocks(N, 128), 128, 0, c->stream>>>(c->d, c->d_perm, grad_caller);
+    k_edge_ref<float><<<blocks(c->d.ne, 128), 128, 0, c->stream>>>(c->d);
+  } else {
+    k_mirrors<double><<<blocks(N, 128), 128, 0, c->stream>>>(c->d, c->d_perm, grad_caller);
+    k_edge_ref<double><<<blocks(c->d.ne, 128), 128, 0, c->stream>>>(c->d);
+  }
   k_reset_stats<<<blocks(c->d.ninst, 128), 128, 0, c->stream>>>(c->d);
   CK(cudaMemsetAsync(c->d.t, 0, sizeof(double) * c->d.ninst, c->stream));
   CK(cudaMemsetAsync(c->d.dt, 0, sizeof(double) * c->d.ninst, c->stream));
   CK(cudaMemsetAsync(c->d.status, 0, sizeof(int), c->stream));
-  k_cfl<<<blocks(c->d.nt, 128), 128, 0, c->stream>>>(c->d, p);
+  k_cfl<<<blocks(N, 128), 128, 0, c->stream>>>(c->d, p);
   CK(cudaGetLastError());
   c->phase = 0;
   c->stages = 0;
@@ -495,32 +581,39 @@ int gks2l_bind(gks2l_ctx *c, void *d_workspace, size_t bytes, void *stream) {
   c->stream = (cudaStream_t)stream;
   layout(c, c->ws);
   const Prep &P = c->prep;
-  std::vector<double> ia(P.nt);
-  for (int j = 0; j < P.nt; j++) ia[j] = 1.0 / P.area[j];
+  std::vector<double> fsl(3 * P.nt), en(2 * (size_t)P.ne);
+  for (int j = 0; j < P.nt; j++)
+    for (int f = 0; f < 3; f++) {
+      int ce = P.cedge[f * P.nt + j];
+      int e = ce >= 0 ? ce : ~ce;
+      fsl[f * P.nt + j] = (ce >= 0 ? 1.0 : -1.0) * P.elen[e] / P.area[j];
+    }
+  for (int e = 0; e < P.ne; e++) { en[e] = P.en0[e]; en[P.ne + e] = P.en1[e]; }
   std::vector<double> xf(4 * kMaxXf, 0.0);
   std::copy(P.xf.begin(), P.xf.end(), xf.begin());
   int rc;
-  if ((rc = upload(c, c->d.inst, P.inst)) || (rc = upload(c, c->d.inv_area, ia)) ||
-      (rc = upload(c, c->d.area, P.area)) || (rc = upload(c, c->d.hs, P.hs)) || (rc = upload(c, c->d.dX, P.dX)) ||
+  if ((rc = upload(c, c->d.inst, P.inst)) || (rc = upload(c, c->d.area, P.area)) ||
+      (rc = upload(c, c->d.hs, P.hs)) || (rc = upload(c, c->d.dX, P.dX)) ||
       (rc = upload(c, c->d.st_cell, P.st_cell)) || (rc = upload(c, c->d.st_xf, P.st_xf)) ||
-      (rc = upload(c, c->d.plane, P.plane)) || (rc = upload(c, c->d.cedge, P.cedge)) ||
+      (rc = upload(c, c->d.cedge, P.cedge)) || (rc = upload(c, c->d.fsl, fsl)) ||
       (rc = upload(c, c->d.inst_first, P.inst_first)) || (rc = upload(c, c->d.eL, P.eL)) ||
-      (rc = upload(c, c->d.eR, P.eR)) || (rc = upload(c, c->d.exf, P.exf)) || (rc = upload(c, c->d.en0, P.en0)) ||
-      (rc = upload(c, c->d.en1, P.en1)) || (rc = upload(c, c->d.elen, P.elen)) || (rc = upload(c, c->d.xf, xf)) ||
+      (rc = upload(c, c->d.eR, P.eR)) || (rc = upload(c, c->d.exf, P.exf)) || (rc = upload(c, c->d.xf, xf)) ||
       (rc = upload(c, c->d_perm, P.perm)))
     return rc;
   if (c->rsize == 4) {
-    std::vector<float> t1, t2, t3, t4, t5, t6;
+    std::vector<float> t1, t2, t3, t4, t5, t6, t7, t8;
     if ((rc = upload_r(c, c->d.lsq, P.lsq, t1)) || (rc = upload_r(c, c->d.p1op, P.p1op, t2)) ||
         (rc = upload_r(c, c->d.bq, P.bq, t3)) || (rc = upload_r(c, c->d.mmean, P.mmean, t4)) ||
-        (rc = upload_r(c, c->d.exiL, P.exiL, t5)) || (rc = upload_r(c, c->d.exiR, P.exiR, t6)))
+        (rc = upload_r(c, c->d.exiL, P.exiL, t5)) || (rc = upload_r(c, c->d.exiR, P.exiR, t6)) ||
+        (rc = upload_r(c, c->d.plane, P.plane, t7)) || (rc = upload_r(c, c->d.en, en, t8)))
       return rc;
     CK(cudaStreamSynchronize(c->stream));
   } else {
     if ((rc = upload(c, c->d.lsq, P.lsq)) || (rc = upload(c, c->d.p1op, P.p1op)) || (rc = upload(c, c->d.bq, P.bq)) ||
         (rc = upload(c, c->d.mmean, P.mmean)) || (rc = upload(c, c->d.exiL, P.exiL)) ||
-        (rc = upload(c, c->d.exiR, P.exiR)))
+        (rc = upload(c, c->d.exiR, P.exiR)) || (rc = upload(c, c->d.plane, P.plane)) || (rc = upload(c, c->d.en, en)))
       return rc;
+    CK(cudaStreamSynchronize(c->stream));
   }
   CK(cudaMemsetAsync(c->d.gate, 0, P.nt, c->stream));
   CK(cudaMemsetAsync(c->d.gate_count, 0, 2 * sizeof(unsigned long long), c->stream));
@@ -534,6 +627,7 @@ int gks2l_set_bathymetry(gks2l_ctx *c, const double *b_vert) {
   if (!c || !b_vert) return GKS2L_EINVAL;
   c->bvert.assign(b_vert, b_vert + c->prep.nv);
   c->has_b = true;
+  c->has_state = false;   // the level mirrors depend on B: set the state again
   if (c->bound) return upload_bathymetry(c);
   return GKS2L_OK;
 }
@@ -545,10 +639,8 @@ int gks2l_set_state(gks2l_ctx *c, const double *avg, const double *grad) {
   CK(cudaMemcpyAsync(c->d_stage, avg, 6 * nt * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   if (grad) CK(cudaMemcpyAsync(c->d_stage + 6 * nt, grad, 12 * nt * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   k_gather<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 6, c->d_perm, c->d_stage, c->d.avg);
-  k_gather<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 12, c->d_perm, grad ? c->d_stage + 6 * nt : nullptr,
-                                                  c->d.grad);
   CK(cudaGetLastError());
-  int rc = after_state(c);
+  int rc = after_state(c, grad ? c->d_stage + 6 * nt : nullptr);
   if (rc) return rc;
   CK(cudaStreamSynchronize(c->stream));   // the host arrays may be released after return
   return GKS2L_OK;
@@ -559,9 +651,8 @@ int gks2l_set_state_device(gks2l_ctx *c, const double *d_avg, const double *d_gr
   if (!c->bound) return GKS2L_ESTATE;
   const size_t nt = c->prep.nt;
   k_gather<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 6, c->d_perm, d_avg, c->d.avg);
-  k_gather<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 12, c->d_perm, d_grad, c->d.grad);
   CK(cudaGetLastError());
-  return after_state(c);
+  return after_state(c, d_grad);
 }
 
 int gks2l_advance(gks2l_ctx *c, int32_t n_stages, double t_end, double *t_out) {
@@ -609,7 +700,10 @@ int gks2l_get_state(gks2l_ctx *c, double *avg, double *grad) {
   if (!c->bound || !c->has_state) return GKS2L_ESTATE;
   const size_t nt = c->prep.nt;
   k_scatter<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 6, c->d_perm, c->d.avg, c->d_stage);
-  k_scatter<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 12, c->d_perm, c->d.grad, c->d_stage + 6 * nt);
+  if (c->par.precision == GKS2L_FP32)
+    k_grad_out<float><<<blocks(nt, 128), 128, 0, c->stream>>>(c->d, c->d_perm, c->d_stage + 6 * nt);
+  else
+    k_grad_out<double><<<blocks(nt, 128), 128, 0, c->stream>>>(c->d, c->d_perm, c->d_stage + 6 * nt);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(avg, c->d_stage, 6 * nt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   if (grad) CK(cudaMemcpyAsync(grad, c->d_stage + 6 * nt, 12 * nt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -622,7 +716,12 @@ int gks2l_get_state_device(gks2l_ctx *c, double *d_avg, double *d_grad) {
   if (!c->bound || !c->has_state) return GKS2L_ESTATE;
   const size_t nt = c->prep.nt;
   k_scatter<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 6, c->d_perm, c->d.avg, d_avg);
-  if (d_grad) k_scatter<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 12, c->d_perm, c->d.grad, d_grad);
+  if (d_grad) {
+    if (c->par.precision == GKS2L_FP32)
+      k_grad_out<float><<<blocks(nt, 128), 128, 0, c->stream>>>(c->d, c->d_perm, d_grad);
+    else
+      k_grad_out<double><<<blocks(nt, 128), 128, 0, c->stream>>>(c->d, c->d_perm, d_grad);
+  }
   CK(cudaGetLastError());
   return GKS2L_OK;
 }
@@ -680,7 +779,8 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[5]) {
       if (f32) k_edge<float><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d, p, stage);
       else k_edge<double><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d, p, stage);
       CK(cudaEventRecord(ev[5], c->stream));
-      k_update<<<blocks(d.nt, 128), 128, 0, c->stream>>>(d, p, stage);
+      if (f32) k_update<float><<<blocks(d.nt, 128), 128, 0, c->stream>>>(d, p, stage);
+      else k_update<double><<<blocks(d.nt, 128), 128, 0, c->stream>>>(d, p, stage);
       CK(cudaEventRecord(ev[6], c->stream));
       CK(cudaEventSynchronize(ev[6]));
       float t;

@@ -4,11 +4,20 @@
 // or a cell) and is written as plain host/device code so the arithmetic of a
 // unit does not depend on the launch shape.
 //
-// Precision: `R` is the type of the deviation arithmetic (double in the FP64
-// form, float in the FP32 form). Cell averages, depths at Gauss points,
-// the hydrostatic parts of the interface solution and every flux/source sum
-// stay in double in both forms, which keeps the rest state exact
-// (Sec. 3.2: balance between the interface flux and the cell sources).
+// Deviation form. Every instance carries two FP64 reference values, R2 (a
+// depth of the upper layer) and R1 (a water level eta1 = h1 + B of the lower
+// layer): the area-weighted means of the state when it was set, rounded to
+// 2^-32. The kernels read and write only deviations from them, of type R
+// (double in the FP64 form, float in the FP32 form): the cell mirrors
+// dq = (h2 - R2, h2U2, h2V2, eta1 - R1, h1U1, h1V1) and gradients
+// dg = grad(h2, h2U2, h2V2, eta1, h1U1, h1V1). At rest (eta1 and h2 constant,
+// Sec. 3.2) every deviation vanishes, so the well-balanced cancellation
+// between the interface flux and the cell sources holds in any precision: the
+// reference pressure G (R1 - B)^2 / 2 of the lower layer is integrated around
+// the cell exactly (B is linear, 2-point Gauss is exact) and combined with the
+// bottom source analytically, leaving -G (eta1_j - R1) grad B_j. FP64 is kept
+// for the cell averages, the mass fluxes and the state update, which keeps
+// each layer's mass exactly conserved.
 #pragma once
 #include <cmath>
 #include <cstdint>
@@ -25,7 +34,7 @@ namespace gks2l {
 using std::isfinite;
 #endif
 
-constexpr int NV = 6;        // h2, h2U2, h2V2, h1 (reconstructed as eta1 = h1 + B), h1U1, h1V1
+constexpr int NV = 6;        // h2, h2U2, h2V2, h1 (as eta1 = h1 + B), h1U1, h1V1
 constexpr int NSLOT = 9;
 constexpr int NCOL = 17;
 constexpr int NCOEF = 10;    // per variable: c0 (value offset) + 9 Taylor coefficients
@@ -35,27 +44,33 @@ struct Dev {
   int nt, ne, ninst;
   // per cell
   const int *inst;
-  const double *inv_area, *area, *hs, *dX;
+  const double *area, *hs, *dX;
   const double *bmean, *bgx, *bgy;
   const int *st_cell;
   const int8_t *st_xf;
   const void *lsq, *p1op, *bq, *mmean;
-  const double *plane;
-  const int *cedge;
+  const void *plane;        // [(f*2+d)][cell] plane operator, type R
+  const int *cedge;         // [f][cell]: edge id, or ~edge when the cell is the R side
+  const double *fsl;        // [f][cell]: sign * |Gamma| / |Omega| (double, mass sums)
   const int *inst_first;
-  double *avg, *grad;       // state [v][cell], [(v*2+d)][cell]
-  double *Wn, *Ln, *Ltn;    // stage snapshot
-  void *coef;               // reconstruction deviations [v*10+k][cell]
+  double *avg;              // state averages [v][cell] (FP64)
+  void *dq, *dg;            // deviation mirrors [6][cell], gradients [12][cell], type R
+  void *hrefc;              // R1 - B_j per cell, type R
+  double *Wn, *Ln, *Ltn;    // stage snapshot (FP64)
+  void *coef;               // reconstruction deviations [v*10+k][cell], type R
   void *omg;                // omega_H / gamma_H of eta1 [0] and h2 [1], type R
   uint8_t *gate;            // 1 = smooth by the learned indicator
   // per edge
   const int *eL, *eR;
   const int8_t *exf;
-  const double *en0, *en1, *elen, *eb0, *eb1;
-  const void *exiL, *exiR;  // [4][edge]
-  double *hc;               // [2][edge]: edge-centre eta1-hat, h2-hat
-  double *eF, *eFt, *eW, *eWt, *eWn;  // [6][edge], Gauss-point sums (weights 1/2)
+  const void *en;           // [2][edge] unit normal from L to R, type R
+  const double *eb0, *eb1;  // B at the two Gauss points
+  const void *exiL, *exiR;  // [4][edge] Gauss points in each side's scaled frame, type R
+  void *hrefe;              // [2][edge] R1 - B at the Gauss points, type R
+  void *hc;                 // [2][edge] edge-centre blended level deviations, type R
+  void *eF, *eFt, *eW, *eWt, *eWn;  // [6][edge] Gauss-point sums (weights 1/2), deviations, type R
   // per instance
+  double *ref;              // [inst*2]: R2, R1
   double *dt, *t;
   unsigned long long *dtbits;
   double *mass;             // [inst*2 + layer]
@@ -65,7 +80,7 @@ struct Dev {
 };
 
 struct Par {
-  double g, chi, cfl, eps, eps_num, gam_hi, weno_eps, t_end;
+  double g, chi, cfl, eps, eps_num, gam_hi, weno_eps;
   int use_gate;
 };
 
@@ -84,6 +99,7 @@ template <> __host__ __device__ __forceinline__ float r_expm1<float>(float x) { 
 template <typename R> __host__ __device__ __forceinline__ R r_sqrt(R x);
 template <> __host__ __device__ __forceinline__ double r_sqrt<double>(double x) { return sqrt(x); }
 template <> __host__ __device__ __forceinline__ float r_sqrt<float>(float x) { return sqrtf(x); }
+template <typename R> __host__ __device__ __forceinline__ R r_abs(R x) { return x < 0 ? -x : x; }
 
 template <typename R>
 __host__ __device__ __forceinline__ void monos(R x, R y, R m[10], R mx[10], R my[10]) {
@@ -97,47 +113,50 @@ __host__ __device__ __forceinline__ void monos(R x, R y, R m[10], R mx[10], R my
   my[6] = 0; my[7] = h * xx; my[8] = xy; my[9] = h * yy;
 }
 
-// ------------------------------------------------------------------ cell data
-// Average of reconstructed variable v of cell c seen through transform code xf
-// (variables: h2, m2x, m2y, eta1 = h1 + B, m1x, m1y).
-__host__ __device__ __forceinline__ double img_avg(const Dev &d, int v, int c, int xf) {
-  const int N = d.nt;
-  if (v == 0) return d.avg[c];
-  if (v == 3) return d.avg[3 * N + c] + d.bmean[c];
-  int b = v < 3 ? 1 : 4;
-  double mx = d.avg[b * N + c], my = d.avg[(b + 1) * N + c];
-  if (xf == 0) return v == b ? mx : my;
-  const double *M = d.xf + 4 * xf;
-  return v == b ? M[0] * mx + M[1] * my : M[2] * mx + M[3] * my;
+template <typename R>
+__host__ __device__ __forceinline__ void rot2(const double *M, R v[2]) {
+  R a = v[0], b = v[1];
+  v[0] = (R)M[0] * a + (R)M[1] * b;
+  v[1] = (R)M[2] * a + (R)M[3] * b;
 }
-__host__ __device__ __forceinline__ void img_grad(const Dev &d, int v, int c, int xf, double g[2]) {
+
+// ------------------------------------------------------------------ cell data
+// Deviation of reconstructed variable v of cell c seen through transform xf.
+template <typename R>
+__host__ __device__ __forceinline__ R img_dq(const Dev &d, int v, int c, int xf) {
   const int N = d.nt;
-  const double *G = d.grad;
-  if (v == 0 || v == 3) {
-    double gx = G[(2 * v) * N + c], gy = G[(2 * v + 1) * N + c];
-    if (v == 3) { gx += d.bgx[c]; gy += d.bgy[c]; }
-    if (xf == 0) { g[0] = gx; g[1] = gy; return; }
-    const double *M = d.xf + 4 * xf;
-    g[0] = M[0] * gx + M[1] * gy;
-    g[1] = M[2] * gx + M[3] * gy;
-    return;
-  }
+  const R *dq = (const R *)d.dq;
+  if (v == 0 || v == 3 || xf == 0) return dq[v * N + c];
   int b = v < 3 ? 1 : 4;
-  int row = v - b;
+  R m[2] = {dq[b * N + c], dq[(b + 1) * N + c]};
+  rot2<R>(d.xf + 4 * xf, m);
+  return m[v - b];
+}
+// gradient of variable v of cell c seen through transform xf
+template <typename R>
+__host__ __device__ __forceinline__ void img_dg(const Dev &d, int v, int c, int xf, R g[2]) {
+  const int N = d.nt;
+  const R *G = (const R *)d.dg;
   if (xf == 0) {
     g[0] = G[(2 * v) * N + c];
     g[1] = G[(2 * v + 1) * N + c];
     return;
   }
-  // momentum gradient tensor T_ik = d m_i / d x_k -> M T M^T
-  double T[2][2] = {{G[(2 * b) * N + c], G[(2 * b + 1) * N + c]},
-                    {G[(2 * b + 2) * N + c], G[(2 * b + 3) * N + c]}};
   const double *M = d.xf + 4 * xf;
-  double Mr[2] = {M[2 * row], M[2 * row + 1]};
+  if (v == 0 || v == 3) {
+    g[0] = G[(2 * v) * N + c];
+    g[1] = G[(2 * v + 1) * N + c];
+    rot2<R>(M, g);
+    return;
+  }
+  // discharge gradient tensor T_ik = d m_i / d x_k -> M T M^T, row v - b
+  int b = v < 3 ? 1 : 4;
+  int row = v - b;
+  R T[2][2] = {{G[(2 * b) * N + c], G[(2 * b + 1) * N + c]}, {G[(2 * b + 2) * N + c], G[(2 * b + 3) * N + c]}};
   for (int k = 0; k < 2; k++) {
-    double s = 0;
+    R s = 0;
     for (int a = 0; a < 2; a++)
-      for (int b2 = 0; b2 < 2; b2++) s += Mr[a] * T[a][b2] * M[2 * k + b2];
+      for (int b2 = 0; b2 < 2; b2++) s += (R)M[2 * row + a] * T[a][b2] * (R)M[2 * k + b2];
     g[k] = s;
   }
 }
@@ -154,21 +173,21 @@ __host__ __device__ inline void recon_unit(const Dev &d, const Par &p, int j, in
   const R *bq = (const R *)d.bq;
   const R *mm = (const R *)d.mmean;
   R *coef = (R *)d.coef;
-  const double q0 = img_avg(d, v, j, 0);
-  const double hs = d.hs[j];
+  const R q0 = ((const R *)d.dq)[v * N + j];
+  const R hs = (R)d.hs[j];
   R rhs[NCOL];
   for (int s = 0; s < NSLOT; s++) {
     int c = d.st_cell[s * N + j];
-    rhs[s] = c >= 0 ? (R)(img_avg(d, v, c, d.st_xf[s * N + j]) - q0) : (R)0;
+    rhs[s] = c >= 0 ? img_dq<R>(d, v, c, d.st_xf[s * N + j]) - q0 : (R)0;
   }
-  double g[2];
-  img_grad(d, v, j, 0, g);
-  rhs[9] = (R)(hs * g[0]);
-  rhs[10] = (R)(hs * g[1]);
+  R g[2];
+  img_dg<R>(d, v, j, 0, g);
+  rhs[9] = hs * g[0];
+  rhs[10] = hs * g[1];
   for (int f = 0; f < 3; f++) {
-    img_grad(d, v, d.st_cell[f * N + j], d.st_xf[f * N + j], g);
-    rhs[11 + 2 * f] = (R)(hs * g[0]);
-    rhs[12 + 2 * f] = (R)(hs * g[1]);
+    img_dg<R>(d, v, d.st_cell[f * N + j], d.st_xf[f * N + j], g);
+    rhs[11 + 2 * f] = hs * g[0];
+    rhs[12 + 2 * f] = hs * g[1];
   }
   R a[9];
   for (int r = 0; r < 9; r++) {
@@ -195,8 +214,12 @@ __host__ __device__ inline void recon_unit(const Dev &d, const Par &p, int j, in
     for (int k = 0; k < 9; k++)
       for (int l = k; l < 9; l++) bh += bq[(idx++) * N + j] * a[k] * a[l];
     beta[0] = bh;
-    R tz = (fabs(bh - beta[1]) + fabs(bh - beta[2]) + fabs(bh - beta[3])) * (R)(1.0 / 3.0);
-    R eps = (R)(p.weno_eps * d.area[j] * (1.0 + q0 * q0));
+    R tz = (r_abs<R>(bh - beta[1]) + r_abs<R>(bh - beta[2]) + r_abs<R>(bh - beta[3])) * (R)(1.0 / 3.0);
+    // the variable's value (reference + deviation) scales the regulariser
+    R Q0 = q0;
+    if (v == 0) Q0 += (R)d.ref[2 * d.inst[j]];
+    if (v == 3) Q0 += (R)d.ref[2 * d.inst[j] + 1];
+    R eps = (R)(p.weno_eps * d.area[j]) * (1 + Q0 * Q0);
     R w[4], ws = 0;
     const R gam[4] = {gh, gl, gl, gl};
     for (int k = 0; k < 4; k++) {
@@ -225,12 +248,11 @@ __host__ __device__ inline void recon_unit(const Dev &d, const Par &p, int j, in
 }
 
 // ------------------------------------------------- evaluation at an edge point
-// Edge-point side data for layer ell (0: lower, reconstructed eta1; 1: upper).
-// Depth and level are double (cell average + polynomial deviation); the
-// discharge, velocities and all gradients are type R.
+// Edge-point side data for layer ell (0: lower, reconstructed eta1; 1: upper),
+// all deviations of type R.
 template <typename R> struct SideVals {
-  double h;       // depth at the point
-  double lev;     // level variable: eta1 (lower) or h2 (upper)
+  R d;            // level deviation at the point (eta1 - R1 or h2 - R2)
+  R h;            // depth at the point (href + d)
   R mx, my;       // discharge
   R gh[2];        // gradient of the depth
   R glev[2];      // gradient of the level variable
@@ -238,20 +260,13 @@ template <typename R> struct SideVals {
   R goth[2];      // gradient of the other layer's level variable
 };
 
+// cell c's reconstruction at scaled point (x, y), seen through transform xf;
+// href is the depth of the reference level at the point
 template <typename R>
-__host__ __device__ __forceinline__ void rot2(const double *M, R v[2]) {
-  R a = v[0], b = v[1];
-  v[0] = (R)M[0] * a + (R)M[1] * b;
-  v[1] = (R)M[2] * a + (R)M[3] * b;
-}
-
-// Values and gradients of the layer's variables and the other layer's level
-// gradient for cell c at scaled point (x, y), seen through transform xf.
-template <typename R>
-__host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, R x, R y, double bq,
-                                          SideVals<R> &s) {
+__host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, R x, R y, R href, SideVals<R> &s) {
   const int N = d.nt;
   const R *coef = (const R *)d.coef;
+  const R *dq = (const R *)d.dq;
   const int v0 = ell == 0 ? 3 : 0, vo = ell == 0 ? 0 : 3;
   R m[10], mx[10], my[10];
   monos<R>(x, y, m, mx, my);
@@ -270,23 +285,16 @@ __host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, 
     gx[i] = ax * ih;
     gy[i] = ay * ih;
   }
-  R gb[2] = {0, 0};
-  if (ell == 0) {
-    gb[0] = (R)d.bgx[c];
-    gb[1] = (R)d.bgy[c];
-    const double a3 = d.avg[3 * N + c];
-    s.h = a3 + (d.bmean[c] - bq) + (double)dev[0];   // h1 = eta1 - B(x)
-    s.lev = (a3 + d.bmean[c]) + (double)dev[0];
-  } else {
-    s.h = d.avg[c] + (double)dev[0];
-    s.lev = s.h;
-  }
-  s.mx = (R)(d.avg[(v0 + 1) * N + c] + (double)dev[1]);
-  s.my = (R)(d.avg[(v0 + 2) * N + c] + (double)dev[2]);
+  s.d = dq[v0 * N + c] + dev[0];
+  s.h = href + s.d;
+  s.mx = dq[(v0 + 1) * N + c] + dev[1];
+  s.my = dq[(v0 + 2) * N + c] + dev[2];
   s.glev[0] = gx[0]; s.glev[1] = gy[0];
   s.gm[0][0] = gx[1]; s.gm[0][1] = gy[1];
   s.gm[1][0] = gx[2]; s.gm[1][1] = gy[2];
   s.goth[0] = gx[3]; s.goth[1] = gy[3];
+  R gb[2] = {0, 0};
+  if (ell == 0) { gb[0] = (R)d.bgx[c]; gb[1] = (R)d.bgy[c]; }
   if (xf != 0) {
     const double *M = d.xf + 4 * xf;
     R mv[2] = {s.mx, s.my};
@@ -304,8 +312,15 @@ __host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, 
         s.gm[i2][k] = acc;
       }
   }
-  s.gh[0] = s.glev[0] - gb[0];
+  s.gh[0] = s.glev[0] - gb[0];   // depth = level - B for the lower layer
   s.gh[1] = s.glev[1] - gb[1];
+}
+
+// depth of the reference level at Gauss point q of edge e for layer ell
+template <typename R>
+__host__ __device__ __forceinline__ R ref_depth(const Dev &d, int ell, int e, int q) {
+  if (ell == 0) return ((const R *)d.hrefe)[q * d.ne + e];
+  return (R)d.ref[2 * d.inst[d.eL[e]]];
 }
 
 // ------------------------------------------------ gas-kinetic interface solution
@@ -386,37 +401,35 @@ __host__ __device__ __forceinline__ void time_ints(R tau, R delta, R q[5]) {
 }
 
 // One layer at one Gauss point, local frame (x along the normal from L to R).
-// Returns the value and time derivative at the stage start of the flux F and
-// of the interface variables W (fit of the two time integrals over delta and
-// delta/2). The hydrostatic parts (h_b and G h_b^2 / 2, h_b = (h_l + h_r)/2)
-// are added in double; everything else is a deviation of type R.
+// Depths h_l = href + dl, h_r = href + dr. Returns the value and time
+// derivative at the stage start of the flux F and of the interface variables
+// W (fit of the two time integrals over delta and delta/2), as deviations:
+// the normal-momentum flux minus G href^2 / 2 and the depth minus href.
 template <typename R>
-__host__ __device__ inline void gks_layer(double hl, double hr, R Ul, R Vl, R Ur, R Vr, const R dnl[3],
+__host__ __device__ inline void gks_layer(R href, R dl, R dr, R Ul, R Vl, R Ur, R Vr, const R dnl[3],
                                           const R dtl[3], const R Dl[2], const R dnr[3], const R dtr[3],
-                                          const R Dr[2], double G, double tau, double delta, double F[3],
-                                          double Ft[3], double W[3], double Wt[3]) {
-  const R g = (R)G;
-  const R hlR = (R)hl, hrR = (R)hr;
+                                          const R Dr[2], R g, R tau, R delta, R F[3], R Ft[3], R W[3], R Wt[3]) {
+  const R hlR = href + dl, hrR = href + dr;
+  const R dlr = dl - dr;                          // h_l - h_r, exact at rest
   const R laml = 1 / (g * hlR), lamr = 1 / (g * hrR);
   const R thl = (R)0.5 * g * hlR, thr = (R)0.5 * g * hrR;
   R mul[6], mur[6], e0l, e0r, El, Er;
   half_moments<R>(Ul, laml, (R)1, mul, e0l, El);
   half_moments<R>(Ur, lamr, (R)-1, mur, e0r, Er);
-  // W-bar: the t = 0 interface state
-  const double hb = 0.5 * (hl + hr);
+  // W-bar: the t = 0 interface state; h_b = (h_l + h_r)/2, h-bar = h_b + hdev
+  const R db = (R)0.5 * (dl + dr);                // h_b - href
+  const R hb = href + db;
   const R hdev = hlR * e0l + hrR * e0r;
-  // h_l E_l - h_r E_r with h E = sqrt(G/(4 pi)) h^{3/2} e^{-lam U^2}: written
-  // through the double difference h_l - h_r so that it vanishes exactly for
-  // equal depths and velocities whatever the rounding or contraction
+  // h_l E_l - h_r E_r with h E = sqrt(G/(4 pi)) h^{3/2} e^{-lam U^2}, written
+  // through h_l - h_r so that it vanishes exactly for equal depths and velocities
   const R xl = r_exp<R>(-laml * Ul * Ul), xr = r_exp<R>(-lamr * Ur * Ur);
   const R sl = r_sqrt<R>(hlR), sr = r_sqrt<R>(hrR);
   const R cphi = r_sqrt<R>(g * (R)(0.25 / 3.14159265358979323846));
-  const R dphi = (R)(hl - hr) * (hlR + sl * sr + hrR) / (sl + sr);
+  const R dphi = dlr * (hlR + sl * sr + hrR) / (sl + sr);
   const R ediff = cphi * (hlR * sl * (xl - xr) + dphi * xr);
   const R mbn = (hlR * Ul * mul[0] + hrR * Ur * mur[0]) + ediff;
   const R mbt = hlR * Vl * mul[0] + hrR * Vr * mur[0];
-  const double hbar = hb + (double)hdev;
-  const R hbR = (R)hbar;
+  const R hbR = hb + hdev;
   const R Ub = mbn / hbR, Vb = mbt / hbR;
   const R lamb = 1 / (g * hbR), thb = (R)0.5 * g * hbR;
   R mbp[6], mbm[6], t0, t1;
@@ -441,27 +454,26 @@ __host__ __device__ inline void gks_layer(double hl, double hr, R Ul, R Vl, R Ur
   kern_moments<R>(kl, mul, thl, Ul, Vl, a);
   kern_moments<R>(kr, mur, thr, Ur, Vr, b);
   for (int k = 0; k < 6; k++) P[4][k] = hlR * a[k] + hrR * b[k];
-  // C1 (full-space moments of g-bar) and C4 (g^l, g^r on their half spaces),
+  // C1 (full-space moments of g-bar) and C4 (g^l, g^r on their half spaces):
   // deviations from the bases h_b and G h_b^2 / 2
   P[0][0] = hdev; P[0][1] = mbn; P[0][2] = mbt;
   P[0][3] = mbn;
-  P[0][4] = mbn * Ub + g * (R)hb * hdev + (R)0.5 * g * hdev * hdev;
+  P[0][4] = mbn * Ub + g * hb * hdev + (R)0.5 * g * hdev * hdev;
   P[0][5] = mbn * Vb;
   P[3][0] = hdev; P[3][1] = mbn; P[3][2] = mbt;
   P[3][3] = mbn;
   {
     const R m2l = thl * e0l - Ul * El, m2r = thr * e0r + Ur * Er;   // mu_2 - th/2 on each side
     P[3][4] = hlR * (Ul * Ul * mul[0] + 2 * Ul * mul[1] + m2l) + hrR * (Ur * Ur * mur[0] + 2 * Ur * mur[1] + m2r) +
-              (R)(0.125 * G * (hl - hr) * (hl - hr));
+              (R)0.125 * g * dlr * dlr;
   }
   P[3][5] = hlR * Vl * (Ul * mul[0] + mul[1]) + hrR * Vr * (Ur * mur[0] + mur[1]);
   // fitted value and derivative at the stage start
   R qd[5], qh[5];
-  const R tauR = (R)tau, dR = (R)delta;
-  time_ints<R>(tauR, dR, qd);
-  time_ints<R>(tauR, (R)0.5 * dR, qh);
+  time_ints<R>(tau, delta, qd);
+  time_ints<R>(tau, (R)0.5 * delta, qh);
   R kv[5], kd[5];
-  const R id = 1 / dR;
+  const R id = 1 / delta;
   for (int i = 0; i < 5; i++) {
     kv[i] = (4 * qh[i] - qd[i]) * id;
     kd[i] = 4 * (qd[i] - 2 * qh[i]) * id * id;
@@ -474,76 +486,77 @@ __host__ __device__ inline void gks_layer(double hl, double hr, R Ul, R Vl, R Ur
       f[k] += kv[i] * P[i][3 + k];
       ft[k] += kd[i] * P[i][3 + k];
     }
-  W[0] = hb + (double)w[0];
-  W[1] = (double)w[1];
-  W[2] = (double)w[2];
-  F[0] = (double)f[0];
-  F[1] = 0.5 * G * hb * hb + (double)f[1];
-  F[2] = (double)f[2];
-  for (int k = 0; k < 3; k++) { Wt[k] = (double)wt[k]; Ft[k] = (double)ft[k]; }
+  // bases relative to the reference: h_b - href and G (h_b^2 - href^2) / 2
+  W[0] = db + w[0];
+  W[1] = w[1];
+  W[2] = w[2];
+  F[0] = f[0];
+  F[1] = (R)0.5 * g * db * (hb + href) + f[1];
+  F[2] = f[2];
+  for (int k = 0; k < 3; k++) { Wt[k] = wt[k]; Ft[k] = ft[k]; }
 }
 
 // ---------------------------------------------------- interface (iface) unit
-// Blended level at one Gauss point of edge e for layer ell (Sec. 2.3):
-// h-hat = xi h^l + (1 - xi) h^r, xi = erfc((U_n^l + U_n^r)/2)/2, with the
-// lower layer blended as the water level eta1 (B is continuous).
+// Blended level deviation at one Gauss point of edge e for layer ell
+// (Sec. 2.3): h-hat = xi h^l + (1 - xi) h^r, xi = erfc((U_n^l + U_n^r)/2)/2;
+// the lower layer is blended as the water level eta1 (B is continuous).
 template <typename R>
-__host__ __device__ inline double iface_unit(const Dev &d, int e, int ell, int q) {
+__host__ __device__ inline R iface_unit(const Dev &d, int e, int ell, int q) {
   const int NE = d.ne;
-  const R *xl = (const R *)d.exiL, *xr = (const R *)d.exiR;
+  const R *xl = (const R *)d.exiL, *xr = (const R *)d.exiR, *en = (const R *)d.en;
   int cL = d.eL[e], cR = d.eR[e], xf = d.exf[e];
-  double bq = q == 0 ? d.eb0[e] : d.eb1[e];
+  const R href = ref_depth<R>(d, ell, e, q);
   SideVals<R> sl, sr;
-  side_vals<R>(d, ell, cL, 0, xl[(2 * q) * NE + e], xl[(2 * q + 1) * NE + e], bq, sl);
-  side_vals<R>(d, ell, cR, xf, xr[(2 * q) * NE + e], xr[(2 * q + 1) * NE + e], bq, sr);
-  const R n0 = (R)d.en0[e], n1 = (R)d.en1[e];
-  R ul = (sl.mx * n0 + sl.my * n1) / (R)sl.h;
-  R ur = (sr.mx * n0 + sr.my * n1) / (R)sr.h;
+  side_vals<R>(d, ell, cL, 0, xl[(2 * q) * NE + e], xl[(2 * q + 1) * NE + e], href, sl);
+  side_vals<R>(d, ell, cR, xf, xr[(2 * q) * NE + e], xr[(2 * q + 1) * NE + e], href, sr);
+  const R n0 = en[e], n1 = en[NE + e];
+  R ul = (sl.mx * n0 + sl.my * n1) / sl.h;
+  R ur = (sr.mx * n0 + sr.my * n1) / sr.h;
   R xi = (R)0.5 * r_erfc<R>((R)0.5 * (ul + ur));
-  return sr.lev + (double)xi * (sl.lev - sr.lev);
+  return sr.d + xi * (sl.d - sr.d);
 }
 
 // plane gradient (Sec. 2.3) of the blended level `which` for cell c
-__host__ __device__ __forceinline__ void plane_grad(const Dev &d, int c, int which, double g[2]) {
+template <typename R>
+__host__ __device__ __forceinline__ void plane_grad(const Dev &d, int c, int which, R g[2]) {
   const int N = d.nt, NE = d.ne;
+  const R *pl = (const R *)d.plane, *hc = (const R *)d.hc;
   g[0] = g[1] = 0;
   for (int f = 0; f < 3; f++) {
     int ce = d.cedge[f * N + c];
     int e = ce >= 0 ? ce : ~ce;
-    double v = d.hc[which * NE + e];
-    g[0] += d.plane[(f * 2) * N + c] * v;
-    g[1] += d.plane[(f * 2 + 1) * N + c] * v;
+    R v = hc[which * NE + e];
+    g[0] += pl[(f * 2) * N + c] * v;
+    g[1] += pl[(f * 2 + 1) * N + c] * v;
   }
 }
 
 // ------------------------------------------------------------- edge unit
 // Interface solution of layer ell at Gauss point q of edge e, global frame:
-// out[0..2] = F, out[3..5] = F_t, out[6..8] = W, out[9..11] = W_t.
+// out[0..2] = F, out[3..5] = F_t, out[6..8] = W, out[9..11] = W_t (deviations).
 template <typename R>
-__host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int ell, int q, int stage,
-                                          double out[12]) {
+__host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int ell, int q, int stage, R out[12]) {
   const int NE = d.ne;
-  const R *xl = (const R *)d.exiL, *xr = (const R *)d.exiR;
+  const R *xl = (const R *)d.exiL, *xr = (const R *)d.exiR, *en = (const R *)d.en;
   int cL = d.eL[e], cR = d.eR[e], xf = d.exf[e];
-  const double dt = d.dt[d.inst[cL]];
-  const double delta = stage == 1 ? dt : 0.5 * dt;
-  double bq = q == 0 ? d.eb0[e] : d.eb1[e];
+  const R dt = (R)d.dt[d.inst[cL]];
+  const R delta = stage == 1 ? dt : (R)0.5 * dt;
+  const R href = ref_depth<R>(d, ell, e, q);
   SideVals<R> s[2];
-  side_vals<R>(d, ell, cL, 0, xl[(2 * q) * NE + e], xl[(2 * q + 1) * NE + e], bq, s[0]);
-  side_vals<R>(d, ell, cR, xf, xr[(2 * q) * NE + e], xr[(2 * q + 1) * NE + e], bq, s[1]);
+  side_vals<R>(d, ell, cL, 0, xl[(2 * q) * NE + e], xl[(2 * q + 1) * NE + e], href, s[0]);
+  side_vals<R>(d, ell, cR, xf, xr[(2 * q) * NE + e], xr[(2 * q + 1) * NE + e], href, s[1]);
   // blended derivative of the other layer's level and the well-balance vector
   // D = grad h - grad Phi / G = grad(level) + c (w grad(other) + (1 - w) grad P1)
   const int oth = 1 - ell;  // hc / omg index of the other layer: 0 = eta1, 1 = h2
   const R *om = (const R *)d.omg;
   R w = om[oth * d.nt + cL] < om[oth * d.nt + cR] ? om[oth * d.nt + cL] : om[oth * d.nt + cR];
   w = w < (R)0 ? (R)0 : (w > (R)1 ? (R)1 : w);
-  double pl0[2], pl1[2];
-  plane_grad(d, cL, oth, pl0);
-  plane_grad(d, cR, oth, pl1);
-  R pl[2][2] = {{(R)pl0[0], (R)pl0[1]}, {(R)pl1[0], (R)pl1[1]}};
+  R pl[2][2];
+  plane_grad<R>(d, cL, oth, pl[0]);
+  plane_grad<R>(d, cR, oth, pl[1]);
   if (xf != 0) rot2<R>(d.xf + 4 * xf, pl[1]);
   const R cf = (R)(ell == 0 ? p.chi : 1.0);
-  const R n0 = (R)d.en0[e], n1 = (R)d.en1[e];
+  const R n0 = en[e], n1 = en[NE + e];
   R U[2], V[2], dn[2][3], dtt[2][3], D[2][2];
   for (int sd = 0; sd < 2; sd++) {
     const SideVals<R> &S = s[sd];
@@ -551,7 +564,7 @@ __host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int
     R Dy = S.glev[1] + cf * (w * S.goth[1] + (1 - w) * pl[sd][1]);
     D[sd][0] = Dx * n0 + Dy * n1;
     D[sd][1] = -Dx * n1 + Dy * n0;
-    R ih = (R)1 / (R)S.h;
+    R ih = (R)1 / S.h;
     U[sd] = (S.mx * n0 + S.my * n1) * ih;
     V[sd] = (-S.mx * n1 + S.my * n0) * ih;
     // derivatives along n and t of (h, m_n, m_t)
@@ -567,22 +580,18 @@ __host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int
       outv[k][2] = -dmx * n1 + dmy * n0;
     }
   }
-  const double hl = s[0].h, hr = s[1].h;
   // collision time (Sec. 4): tau = eps dt + eps_num |(hl^2 - hr^2)/(hl^2 + hr^2)| dt
-  const R dlr = (R)(hl - hr), slr = (R)(hl + hr);
-  const R hl2 = (R)hl * (R)hl, hr2 = (R)hr * (R)hr;
-  R jump = dlr * slr / (hl2 + hr2);
-  jump = jump < 0 ? -jump : jump;
-  const double tau = (double)((R)p.eps * (R)dt + (R)p.eps_num * jump * (R)dt);
-  double F[3], Ft[3], W[3], Wt[3];
-  gks_layer<R>(hl, hr, U[0], V[0], U[1], V[1], dn[0], dtt[0], D[0], dn[1], dtt[1], D[1], p.g, tau, delta, F, Ft,
-               W, Wt);
-  const double dn0 = d.en0[e], dn1 = d.en1[e];
-  const double *src[4] = {F, Ft, W, Wt};
+  const R hl = s[0].h, hr = s[1].h;
+  const R jump = r_abs<R>((s[0].d - s[1].d) * (hl + hr) / (hl * hl + hr * hr));
+  const R tau = (R)p.eps * dt + (R)p.eps_num * jump * dt;
+  R F[3], Ft[3], W[3], Wt[3];
+  gks_layer<R>(href, s[0].d, s[1].d, U[0], V[0], U[1], V[1], dn[0], dtt[0], D[0], dn[1], dtt[1], D[1], (R)p.g,
+               tau, delta, F, Ft, W, Wt);
+  const R *src[4] = {F, Ft, W, Wt};
   for (int k = 0; k < 4; k++) {
     out[3 * k] = src[k][0];
-    out[3 * k + 1] = src[k][1] * dn0 - src[k][2] * dn1;
-    out[3 * k + 2] = src[k][1] * dn1 + src[k][2] * dn0;
+    out[3 * k + 1] = src[k][1] * n0 - src[k][2] * n1;
+    out[3 * k + 2] = src[k][1] * n1 + src[k][2] * n0;
   }
 }
 
@@ -590,81 +599,101 @@ __host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int
 // Flux and source residuals, S2O4 update (Eq. SWE-fully-discrete), interface
 // values at the stage end (Eq. S2O3) and Gauss-theorem gradients (Eq. slope-1).
 // Returns the CFL ratio dX/U_max of the new state (stage 2) or 0.
+template <typename R>
 __host__ __device__ inline double update_unit(const Dev &d, const Par &p, int j, int stage, int *flags) {
   const int N = d.nt, NE = d.ne;
-  const double dt = d.dt[d.inst[j]];
+  const int in = d.inst[j];
+  const double dt = d.dt[in];
   if (!(dt > 0)) return 0;
-  const double ia = d.inv_area[j];
-  double LF[NV] = {0}, LFt[NV] = {0}, mW[NV] = {0}, mWt[NV] = {0};
-  double GG[NV][2] = {{0}}, GGt[NV][2] = {{0}}, GGn[NV][2] = {{0}};
-  const double *Wcur = stage == 1 ? d.eWn : d.eW;
-  const double cend = stage == 1 ? 0.5 * dt : dt;
+  const R *eF = (const R *)d.eF, *eFt = (const R *)d.eFt, *eWt = (const R *)d.eWt, *eWn = (const R *)d.eWn;
+  const R *Wcur = stage == 1 ? eWn : (const R *)d.eW;
+  const R *en = (const R *)d.en;
+  const R cend = (R)(stage == 1 ? 0.5 * dt : dt);
+  // mass residuals in FP64 (exact conservation), the rest in R
+  double LFm[2] = {0, 0}, LFtm[2] = {0, 0};
+  R LF[NV] = {0}, LFt[NV] = {0}, mW[NV] = {0}, mWt[NV] = {0};
+  R GG[NV][2] = {{0}}, GGt[NV][2] = {{0}}, GGn[NV][2] = {{0}};
   for (int f = 0; f < 3; f++) {
     int ce = d.cedge[f * N + j];
-    double sg = ce >= 0 ? 1.0 : -1.0;
     int e = ce >= 0 ? ce : ~ce;
-    double sl = sg * d.elen[e] * ia;
-    double nx = d.en0[e], ny = d.en1[e];
+    const double sl = d.fsl[f * N + j];
+    const R slR = (R)sl;
+    const R nx = en[e], ny = en[NE + e];
     for (int v = 0; v < NV; v++) {
-      double F = d.eF[v * NE + e], Ft = d.eFt[v * NE + e];
-      double W = Wcur[v * NE + e], Wt = d.eWt[v * NE + e], Wn = d.eWn[v * NE + e];
-      LF[v] -= sl * F;
-      LFt[v] -= sl * Ft;
-      mW[v] += W * (1.0 / 3.0);
-      mWt[v] += Wt * (1.0 / 3.0);
-      GG[v][0] += sl * nx * W; GG[v][1] += sl * ny * W;
-      GGt[v][0] += sl * nx * Wt; GGt[v][1] += sl * ny * Wt;
-      double We = Wn + cend * Wt;
-      GGn[v][0] += sl * nx * We; GGn[v][1] += sl * ny * We;
+      R F = eF[v * NE + e], Ft = eFt[v * NE + e];
+      R W = Wcur[v * NE + e], Wt = eWt[v * NE + e], Wn = eWn[v * NE + e];
+      if (v == 0 || v == 3) {
+        LFm[v / 3] -= sl * (double)F;
+        LFtm[v / 3] -= sl * (double)Ft;
+      } else {
+        LF[v] -= slR * F;
+        LFt[v] -= slR * Ft;
+      }
+      mW[v] += W * (R)(1.0 / 3.0);
+      mWt[v] += Wt * (R)(1.0 / 3.0);
+      R snx = slR * nx, sny = slR * ny;
+      GG[v][0] += snx * W; GG[v][1] += sny * W;
+      GGt[v][0] += snx * Wt; GGt[v][1] += sny * Wt;
+      R We = Wn + cend * Wt;
+      GGn[v][0] += snx * We; GGn[v][1] += sny * We;
     }
   }
-  const double G = p.g;
-  const double gb[2] = {d.bgx[j], d.bgy[j]};
-  double L[NV], Lt[NV], a[NV];
-  for (int v = 0; v < NV; v++) { L[v] = LF[v]; Lt[v] = LFt[v]; a[v] = d.avg[v * N + j]; }
-  for (int l = 0; l < 2; l++) {
-    int b = 3 * l;
-    for (int k = 0; k < 2; k++) {
-      L[b + 1 + k] -= G * a[b] * gb[k];
-      Lt[b + 1 + k] -= G * LF[b] * gb[k];
-    }
-  }
+  const R G = (R)p.g, chi = (R)p.chi;
+  const R gb[2] = {(R)d.bgx[j], (R)d.bgy[j]};
+  const R *dq = (const R *)d.dq;
+  const R R2 = (R)d.ref[2 * in];
+  const R hrc = ((const R *)d.hrefc)[j];          // R1 - B_j
+  const R m1 = hrc + mW[3], m2 = R2 + mW[0];       // means of h1, h2 over the 6 Gauss points
+  const R LFh2 = (R)LFm[0], LFh1 = (R)LFm[1];
+  R L[NV], Lt[NV];
   for (int k = 0; k < 2; k++) {
-    L[1 + k] -= G * mW[0] * GG[3][k];
-    Lt[1 + k] -= G * (mWt[0] * GG[3][k] + mW[0] * GGt[3][k]);
-    L[4 + k] -= p.chi * G * mW[3] * GG[0][k];
-    Lt[4 + k] -= p.chi * G * (mWt[3] * GG[0][k] + mW[3] * GGt[0][k]);
+    // upper layer: -G h2 grad(B + h1) with the interface h1 = eta1 - B
+    L[1 + k] = LF[1 + k] - G * (dq[j] - mW[0]) * gb[k] - G * m2 * GG[3][k];
+    Lt[1 + k] = LFt[1 + k] - G * (LFh2 - mWt[0]) * gb[k] - G * mWt[0] * GG[3][k] - G * m2 * GGt[3][k];
+    // lower layer: flux reference pressure + bottom source -> -G (eta1 - R1) grad B; interlayer -chi G h1 grad h2
+    L[4 + k] = LF[4 + k] - G * dq[3 * N + j] * gb[k] - chi * G * m1 * GG[0][k];
+    Lt[4 + k] = LFt[4 + k] - G * LFh1 * gb[k] - chi * G * (mWt[3] * GG[0][k] + m1 * GGt[0][k]);
   }
+  double Ld[NV], Ltd[NV];
+  Ld[0] = LFm[0]; Ltd[0] = LFtm[0];
+  Ld[3] = LFm[1]; Ltd[3] = LFtm[1];
+  const int mom[4] = {1, 2, 4, 5};
+  for (int i = 0; i < 4; i++) { Ld[mom[i]] = (double)L[mom[i]]; Ltd[mom[i]] = (double)Lt[mom[i]]; }
   double nw[NV];
   for (int v = 0; v < NV; v++) {
+    double a = d.avg[v * N + j];
     if (stage == 1) {
-      d.Wn[v * N + j] = a[v];
-      d.Ln[v * N + j] = L[v];
-      d.Ltn[v * N + j] = Lt[v];
-      nw[v] = a[v] + 0.5 * dt * L[v] + 0.125 * dt * dt * Lt[v];
+      d.Wn[v * N + j] = a;
+      d.Ln[v * N + j] = Ld[v];
+      d.Ltn[v * N + j] = Ltd[v];
+      nw[v] = a + 0.5 * dt * Ld[v] + 0.125 * dt * dt * Ltd[v];
     } else {
       nw[v] = d.Wn[v * N + j] + dt * d.Ln[v * N + j] + dt * dt * (1.0 / 6.0) * d.Ltn[v * N + j] +
-              dt * dt * (1.0 / 3.0) * Lt[v];
+              dt * dt * (1.0 / 3.0) * Ltd[v];
     }
   }
+  R *dqw = (R *)d.dq, *dgw = (R *)d.dg;
   for (int v = 0; v < NV; v++) {
     d.avg[v * N + j] = nw[v];
-    d.grad[(2 * v) * N + j] = GGn[v][0];
-    d.grad[(2 * v + 1) * N + j] = GGn[v][1];
+    dgw[(2 * v) * N + j] = GGn[v][0];
+    dgw[(2 * v + 1) * N + j] = GGn[v][1];
   }
+  dqw[j] = (R)(nw[0] - d.ref[2 * in]);
+  dqw[3 * N + j] = (R)((nw[3] + d.bmean[j]) - d.ref[2 * in + 1]);
+  for (int i = 0; i < 4; i++) dqw[mom[i] * N + j] = (R)nw[mom[i]];
   int fl = 0;
   for (int v = 0; v < NV; v++)
     if (!isfinite(nw[v]) || !isfinite(GGn[v][0]) || !isfinite(GGn[v][1])) fl |= 2;
   if (!(nw[0] > 0) || !(nw[3] > 0)) fl |= 1;
   *flags = fl;
   if (stage != 2) return 0;
-  double um = 0;
+  R um = 0;
   for (int l = 0; l < 2; l++) {
-    double h = nw[3 * l], u = nw[3 * l + 1] / h, v = nw[3 * l + 2] / h;
-    double sp = sqrt(u * u + v * v) + sqrt(G * h);
+    R h = (R)nw[3 * l], u = (R)nw[3 * l + 1] / h, v = (R)nw[3 * l + 2] / h;
+    R sp = r_sqrt<R>(u * u + v * v) + r_sqrt<R>(G * h);
     um = sp > um ? sp : um;
   }
-  return d.dX[j] / um;
+  return d.dX[j] / (double)um;
 }
 
 }  // namespace gks2l
