@@ -45,7 +45,7 @@ N_SQ = 1024
 # move with the structure-of-arrays layout (each cell or edge record read or
 # written once). Units: cells for recon and update, edges for iface and edge.
 WORK_PER_UNIT = {
-    "fp32": {"recon": (3830, 236, 1417), "iface": (878, 56, 277), "edge": (6646, 436, 514),
+    "fp32": {"recon": (4021, 0, 1417), "iface": (928, 0, 277), "edge": (6981, 0, 514),
              "update": (0, 343, 850)},
     "fp64": {"recon": (69, 4593, 2209), "iface": (15, 1349, 473), "edge": (107, 9162, 696),
              "update": (0, 343, 850)},
@@ -54,7 +54,7 @@ WORK_PER_UNIT = {
 PEAK_TFLOPS = {"fp32": 76.5, "fp64": 1.254}
 # DRAM bytes per unit (dram__bytes_read.sum + dram__bytes_write.sum of one
 # launch on the 131,072-cell case, per unit; traffic grows with the units).
-TRAFFIC_PER_UNIT = {"fp32": {"recon": 1318.0, "iface": 277.0, "edge": 416.0, "update": 431.0}}
+TRAFFIC_PER_UNIT = {"fp32": {"recon": 1174.0, "iface": 235.0, "edge": 293.0, "update": 431.0}}
 
 
 def roofline(form, kernel, units, ms, hbm_gbs):

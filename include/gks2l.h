@@ -45,6 +45,7 @@ extern "C" {
 #define GKS2L_ESPACE -7      /* workspace too small                                 */
 #define GKS2L_ENOTIMPL -8
 #define GKS2L_ETOOBIG -9     /* size beyond a fixed maximum (gks2l_cfl_mass_noalloc) */
+#define GKS2L_ETIMEOUT -10   /* a bounded device wait (TMA staging) gave up        */
 
 /* boundary kinds per triangle edge (edge k runs from tri[k] to tri[(k+1)%3]) */
 #define GKS2L_BC_INTERIOR 0

@@ -2,13 +2,17 @@
 //
 // One S2O4 stage (arXiv 2306.04467, Eq. SWE-fully-discrete) is four kernels
 // over structure-of-arrays data in a Morton-renumbered cell order:
-//   k_recon   (cell x variable)      compact P3/WENO reconstruction (Sec. 3.4)
+//   k_recon   (32 cells x 6 variables per block) compact P3/WENO reconstruction
+//             (Sec. 3.4); the block's operator rows are staged into shared
+//             memory by TMA (cp.async.bulk.tensor) behind an mbarrier
 //   k_iface   (edge x layer x point) blended interface levels h-hat (Sec. 2.3)
 //   k_edge    (edge x layer x point) gas-kinetic interface solution (Eq. SWE-2nd-order)
 //   k_update  (cell)                 fluxes, sources, S2O4 update, Gauss-theorem
 //                                    gradients (Eqs. SWE-semi-flux, slope-1, S2O3),
 //                                    CFL and conservation reductions
 // A step is k_step_begin + two stages, captured once into a CUDA graph.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,14 +32,103 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr unsigned long long DBL_INF_BITS = 0x7FF0000000000000ull;
+constexpr int TW = 32;                  // cells per reconstruction tile
+constexpr int ST_TIMEOUT = 4;           // status bit: a bounded wait gave up
+
+// ---------------------------------------------------------------- TMA staging
+// Operator rows of one tile of TW cells in shared memory, [row][TW] each.
+struct ReconMaps {
+  CUtensorMap lsq, p1, bq, mm, st, sx;
+};
+
+template <typename R> struct TileLayout {
+  static constexpr unsigned LSQ = 0;
+  static constexpr unsigned P1 = LSQ + kCoef * kCols * TW * sizeof(R);
+  static constexpr unsigned BQ = P1 + 30 * TW * sizeof(R);
+  static constexpr unsigned MM = BQ + kBeta * TW * sizeof(R);
+  static constexpr unsigned ST = MM + 7 * TW * sizeof(R);
+  static constexpr unsigned SX = ST + kSlots * TW * 4;
+  static constexpr unsigned BAR = SX + 384;                   // 9 * 32 int8 rounded to 128 B
+  static constexpr unsigned BYTES = BAR + 16;
+  static constexpr unsigned TX = BAR - 96;                    // bytes the six copies deliver
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, void *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(dst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(void *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for phase 0 of an mbarrier for at most ~limit_ns
+__device__ __forceinline__ bool mbar_wait_bounded(void *bar, unsigned long long limit_ns) {
+  unsigned long long t0 = global_ns();
+  for (int it = 0; it < (1 << 24); it++) {
+    if (mbar_try_wait(bar, 0)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
 
 // ------------------------------------------------------------------ kernels
 template <typename R>
-__global__ void __launch_bounds__(192) k_recon(Dev d, Par p) {
-  int j = blockIdx.x * 32 + threadIdx.x;
+__global__ void __launch_bounds__(192) k_recon(Dev d, Par p, const __grid_constant__ ReconMaps maps) {
+  using T = TileLayout<R>;
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int j0 = blockIdx.x * TW;
+  void *bar = sm + T::BAR;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(T::TX)
+                 : "memory");
+    tma_load_2d(sm + T::LSQ, &maps.lsq, j0, 0, bar);
+    tma_load_2d(sm + T::P1, &maps.p1, j0, 0, bar);
+    tma_load_2d(sm + T::BQ, &maps.bq, j0, 0, bar);
+    tma_load_2d(sm + T::MM, &maps.mm, j0, 0, bar);
+    tma_load_2d(sm + T::ST, &maps.st, j0, 0, bar);
+    tma_load_2d(sm + T::SX, &maps.sx, j0, 0, bar);
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(bar, 1000000000ull)) {
+    // the copies did not land within a second: report, wait for them once
+    // more (bounded) so no copy outlives the block, and leave
+    if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(d.status, ST_TIMEOUT);
+    mbar_wait_bounded(bar, 1000000000ull);
+    return;
+  }
+  const int j = j0 + threadIdx.x;
   if (j >= d.nt) return;
   if (!(d.dt[d.inst[j]] > 0)) return;
-  recon_unit<R>(d, p, j, threadIdx.y);
+  CellOps<R> o;
+  o.lsq = (const R *)(sm + T::LSQ);
+  o.p1 = (const R *)(sm + T::P1);
+  o.bq = (const R *)(sm + T::BQ);
+  o.mm = (const R *)(sm + T::MM);
+  o.st = (const int *)(sm + T::ST);
+  o.sx = (const int8_t *)(sm + T::SX);
+  o.stride = TW;
+  o.idx = threadIdx.x;
+  recon_unit<R>(d, p, o, j, threadIdx.y);
 }
 
 template <typename R>
@@ -128,7 +221,7 @@ __global__ void __launch_bounds__(128) k_update(Dev d, Par p, int stage) {
   if (stage != 2) return;
   double m1 = 0, m2 = 0;
   if (ok) {
-    m1 = d.area[j] * d.avg[3 * d.nt + j];
+    m1 = d.area[j] * d.avg[3 * d.cs + j];
     m2 = d.area[j] * d.avg[j];
   }
   reduce_cell_stats(d, ok, inst, ratio, m1, m2);
@@ -144,8 +237,8 @@ __global__ void __launch_bounds__(128) k_cfl(Dev d, Par p) {
   if (ok) {
     double um = 0;
     for (int l = 0; l < 2; l++) {
-      double h = d.avg[(3 * l) * d.nt + j];
-      double u = d.avg[(3 * l + 1) * d.nt + j] / h, v = d.avg[(3 * l + 2) * d.nt + j] / h;
+      double h = d.avg[(3 * l) * d.cs + j];
+      double u = d.avg[(3 * l + 1) * d.cs + j] / h, v = d.avg[(3 * l + 2) * d.cs + j] / h;
       double sp = sqrt(u * u + v * v) + sqrt(p.g * h);
       um = fmax(um, sp);
     }
@@ -154,7 +247,7 @@ __global__ void __launch_bounds__(128) k_cfl(Dev d, Par p) {
       atomicOr(d.status, 2);
       ratio = INFINITY;
     }
-    m1 = d.area[j] * d.avg[3 * d.nt + j];
+    m1 = d.area[j] * d.avg[3 * d.cs + j];
     m2 = d.area[j] * d.avg[j];
   }
   reduce_cell_stats(d, ok, inst, ratio, m1, m2);
@@ -169,6 +262,7 @@ __global__ void k_reset_stats(Dev d) {
 
 // step size of each instance from the CFL ratio of the current state (Sec. 4),
 // shortened to land on t_end
+template <typename R>
 __global__ void k_step_begin(Dev d, Par p, const double *tend) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.ninst) return;
@@ -185,6 +279,7 @@ __global__ void k_step_begin(Dev d, Par p, const double *tend) {
     dt = 0;
   }
   d.dt[i] = dt;
+  ((R *)d.dtR)[i] = (R)dt;
   d.dtbits[i] = DBL_INF_BITS;
   d.mass[2 * i] = d.mass[2 * i + 1] = 0;
 }
@@ -195,14 +290,14 @@ template <typename R>
 __global__ void k_mirrors(Dev d, const int *perm, const double *grad_caller) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= d.nt) return;
-  const int N = d.nt, in = d.inst[j], c = perm[j];
+  const int N = d.cs, in = d.inst[j], c = perm[j];
   R *dq = (R *)d.dq, *dg = (R *)d.dg;
   const double R2 = d.ref[2 * in], R1 = d.ref[2 * in + 1];
   dq[j] = (R)(d.avg[j] - R2);
   dq[3 * N + j] = (R)((d.avg[3 * N + j] + d.bmean[j]) - R1);
   for (int v : {1, 2, 4, 5}) dq[v * N + j] = (R)d.avg[v * N + j];
   for (int k = 0; k < 12; k++) {
-    double gk = grad_caller ? grad_caller[(size_t)k * N + c] : 0.0;
+    double gk = grad_caller ? grad_caller[(size_t)k * d.nt + c] : 0.0;
     if (k == 6) gk += d.bgx[j];
     if (k == 7) gk += d.bgy[j];
     dg[k * N + j] = (R)gk;
@@ -224,28 +319,28 @@ template <typename R>
 __global__ void k_grad_out(Dev d, const int *perm, double *out) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= d.nt) return;
-  const int N = d.nt, c = perm[j];
+  const int c = perm[j];
   const R *dg = (const R *)d.dg;
   for (int k = 0; k < 12; k++) {
-    double gk = (double)dg[k * N + j];
+    double gk = (double)dg[k * d.cs + j];
     if (k == 6) gk -= d.bgx[j];
     if (k == 7) gk -= d.bgy[j];
-    out[(size_t)k * N + c] = gk;
+    out[(size_t)k * d.nt + c] = gk;
   }
 }
 
-// caller order <-> device order
-__global__ void k_gather(int nt, int nvar, const int *perm, const double *src, double *dst) {
+// caller order (stride nt) <-> device order (stride cs)
+__global__ void k_gather(int nt, int cs, int nvar, const int *perm, const double *src, double *dst) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nt) return;
   int c = perm[j];
-  for (int v = 0; v < nvar; v++) dst[(size_t)v * nt + j] = src ? src[(size_t)v * nt + c] : 0.0;
+  for (int v = 0; v < nvar; v++) dst[(size_t)v * cs + j] = src ? src[(size_t)v * nt + c] : 0.0;
 }
-__global__ void k_scatter(int nt, int nvar, const int *perm, const double *src, double *dst) {
+__global__ void k_scatter(int nt, int cs, int nvar, const int *perm, const double *src, double *dst) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nt) return;
   int c = perm[j];
-  for (int v = 0; v < nvar; v++) dst[(size_t)v * nt + c] = src[(size_t)v * nt + j];
+  for (int v = 0; v < nvar; v++) dst[(size_t)v * nt + c] = src[(size_t)v * cs + j];
 }
 
 // FMA-chain throughput probe for the roofline denominators (measurement only)
@@ -284,10 +379,12 @@ struct gks2l_ctx {
   std::vector<double> bvert;
   bool has_b = false, bound = false, has_state = false;
   size_t rsize = 8;
+  int cs = 0;                  // padded cell stride
   char *ws = nullptr;
   size_t ws_bytes = 0;
   cudaStream_t stream = nullptr;
   Dev d{};
+  ReconMaps maps{};
   int *d_perm = nullptr;
   double *d_tend = nullptr;
   double *d_stage = nullptr;   // 18 * nt staging for permutations
@@ -304,35 +401,41 @@ namespace {
 size_t layout(gks2l_ctx *c, char *base) {
   const Prep &P = c->prep;
   const size_t nt = P.nt, ne = P.ne, ni = P.ninst, rs = c->rsize;
+  const size_t cs = (nt + TW - 1) / TW * TW + TW;   // one spare tile keeps every TMA box in bounds
+  c->cs = (int)cs;
   Carver k{base};
   Dev &d = c->d;
-  d.nt = P.nt; d.ne = P.ne; d.ninst = P.ninst;
+  d.nt = P.nt; d.ne = P.ne; d.ninst = P.ninst; d.cs = (int)cs;
   d.inst = k.take<int>(nt);
   d.area = k.take<double>(nt);
   d.hs = k.take<double>(nt);
   d.dX = k.take<double>(nt);
+  d.hsR = k.take<char>(rs * nt);
+  d.ihsR = k.take<char>(rs * nt);
+  d.epsA = k.take<char>(rs * nt);
+  d.bgR = k.take<char>(rs * 2 * cs);
   d.bmean = k.take<double>(nt);
   d.bgx = k.take<double>(nt);
   d.bgy = k.take<double>(nt);
-  d.st_cell = k.take<int>(kSlots * nt);
-  d.st_xf = k.take<int8_t>(kSlots * nt);
-  d.lsq = k.take<char>(rs * kCoef * kCols * nt);
-  d.p1op = k.take<char>(rs * 30 * nt);
-  d.bq = k.take<char>(rs * kBeta * nt);
-  d.mmean = k.take<char>(rs * 7 * nt);
-  d.plane = k.take<char>(rs * 6 * nt);
-  d.cedge = k.take<int>(3 * nt);
-  d.fsl = k.take<double>(3 * nt);
+  d.st_cell = k.take<int>(kSlots * cs);
+  d.st_xf = k.take<int8_t>(kSlots * cs);
+  d.lsq = k.take<char>(rs * kCoef * kCols * cs);
+  d.p1op = k.take<char>(rs * 30 * cs);
+  d.bq = k.take<char>(rs * kBeta * cs);
+  d.mmean = k.take<char>(rs * 7 * cs);
+  d.plane = k.take<char>(rs * 6 * cs);
+  d.cedge = k.take<int>(3 * cs);
+  d.fsl = k.take<double>(3 * cs);
   d.inst_first = k.take<int>(ni + 1);
-  d.avg = k.take<double>(6 * nt);
-  d.dq = k.take<char>(rs * 6 * nt);
-  d.dg = k.take<char>(rs * 12 * nt);
+  d.avg = k.take<double>(6 * cs);
+  d.dq = k.take<char>(rs * 6 * cs);
+  d.dg = k.take<char>(rs * 12 * cs);
   d.hrefc = k.take<char>(rs * nt);
-  d.Wn = k.take<double>(6 * nt);
-  d.Ln = k.take<double>(6 * nt);
-  d.Ltn = k.take<double>(6 * nt);
-  d.coef = k.take<char>(rs * 60 * nt);
-  d.omg = k.take<char>(rs * 2 * nt);
+  d.Wn = k.take<double>(6 * cs);
+  d.Ln = k.take<double>(6 * cs);
+  d.Ltn = k.take<double>(6 * cs);
+  d.coef = k.take<char>(rs * 60 * cs);
+  d.omg = k.take<char>(rs * 2 * cs);
   d.gate = k.take<uint8_t>(nt);
   d.eL = k.take<int>(ne);
   d.eR = k.take<int>(ne);
@@ -350,7 +453,9 @@ size_t layout(gks2l_ctx *c, char *base) {
   d.eWt = k.take<char>(rs * 6 * ne);
   d.eWn = k.take<char>(rs * 6 * ne);
   d.ref = k.take<double>(2 * ni);
+  d.refR = k.take<char>(rs * 2 * ni);
   d.dt = k.take<double>(ni);
+  d.dtR = k.take<char>(rs * ni);
   d.t = k.take<double>(ni);
   d.dtbits = k.take<unsigned long long>(ni);
   d.mass = k.take<double>(2 * ni);
@@ -376,23 +481,37 @@ template <typename T>
 int upload(gks2l_ctx *c, const void *dst, const std::vector<T> &src) {
   if (src.empty()) return 0;
   CK(cudaMemcpyAsync((void *)dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));   // src may be a temporary
   return 0;
 }
-template <typename R>
-int upload_r(gks2l_ctx *c, const void *dst, const std::vector<double> &src, std::vector<R> &tmp) {
-  tmp.assign(src.begin(), src.end());
+// [rows][nt] host array -> [rows][cs] device array of type T (padding zeroed)
+template <typename T, typename S>
+int upload_rows(gks2l_ctx *c, const void *dst, const std::vector<S> &src, int rows) {
+  const size_t nt = c->prep.nt, cs = c->cs;
+  std::vector<T> tmp(rows * cs, (T)0);
+  for (int r = 0; r < rows; r++)
+    for (size_t j = 0; j < nt; j++) tmp[r * cs + j] = (T)src[r * nt + j];
   return upload(c, dst, tmp);
+}
+// a double host array in the form's precision (single row or [rows][cs])
+int upload_form(gks2l_ctx *c, const void *dst, const std::vector<double> &src, int rows, bool padded) {
+  if (padded) return c->rsize == 4 ? upload_rows<float>(c, dst, src, rows) : upload_rows<double>(c, dst, src, rows);
+  if (c->rsize == 4) return upload(c, dst, std::vector<float>(src.begin(), src.end()));
+  return upload(c, dst, src);
 }
 
 int upload_bathymetry(gks2l_ctx *c) {
   std::vector<double> bm, bx, by, e0, e1;
   bathymetry(c->prep, c->has_b ? c->bvert.data() : nullptr, bm, bx, by, e0, e1);
   c->bmean_h = bm;
+  std::vector<double> bg(2 * (size_t)c->prep.nt);
+  std::copy(bx.begin(), bx.end(), bg.begin());
+  std::copy(by.begin(), by.end(), bg.begin() + c->prep.nt);
   int rc;
   if ((rc = upload(c, c->d.bmean, bm)) || (rc = upload(c, c->d.bgx, bx)) || (rc = upload(c, c->d.bgy, by)) ||
-      (rc = upload(c, c->d.eb0, e0)) || (rc = upload(c, c->d.eb1, e1)))
+      (rc = upload(c, c->d.eb0, e0)) || (rc = upload(c, c->d.eb1, e1)) ||
+      (rc = upload_form(c, c->d.bgR, bg, 2, true)))
     return rc;
-  CK(cudaStreamSynchronize(c->stream));
   return 0;
 }
 
@@ -401,17 +520,65 @@ Par make_par(const gks2l_ctx *c) {
   p.g = c->par.g; p.chi = c->par.chi; p.cfl = c->par.cfl;
   p.eps = c->par.eps; p.eps_num = c->par.eps_num;
   p.gam_hi = c->par.weno_gamma_hi; p.weno_eps = c->par.weno_eps;
+  p.gf = (float)p.g; p.chif = (float)p.chi; p.epsf = (float)p.eps; p.eps_numf = (float)p.eps_num;
+  p.gam_hif = (float)p.gam_hi;
   p.use_gate = c->par.indicator == GKS2L_INDICATOR_MLP ? 1 : 0;
   return p;
 }
 
 inline unsigned blocks(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
+// tensor maps of the per-cell operator rows ([rows][cs], tiles of TW cells)
+int make_maps(gks2l_ctx *c) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      c->err = "cuTensorMapEncodeTiled not available";
+      return GKS2L_ECUDA;
+    }
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const bool f32 = c->rsize == 4;
+  auto one = [&](CUtensorMap *m, const void *base, CUtensorMapDataType t, size_t esize, unsigned rows) -> int {
+    cuuint64_t dims[2] = {(cuuint64_t)c->cs, rows};
+    cuuint64_t strides[1] = {(cuuint64_t)c->cs * esize};
+    cuuint32_t box[2] = {(cuuint32_t)TW, rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = encode(m, t, 2, (void *)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      c->err = "cuTensorMapEncodeTiled failed";
+      return GKS2L_ECUDA;
+    }
+    return 0;
+  };
+  const CUtensorMapDataType rt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const size_t rs = c->rsize;
+  int rc;
+  if ((rc = one(&c->maps.lsq, c->d.lsq, rt, rs, kCoef * kCols)) || (rc = one(&c->maps.p1, c->d.p1op, rt, rs, 30)) ||
+      (rc = one(&c->maps.bq, c->d.bq, rt, rs, kBeta)) || (rc = one(&c->maps.mm, c->d.mmean, rt, rs, 7)) ||
+      (rc = one(&c->maps.st, c->d.st_cell, CU_TENSOR_MAP_DATA_TYPE_INT32, 4, kSlots)) ||
+      (rc = one(&c->maps.sx, c->d.st_xf, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, kSlots)))
+    return rc;
+  return 0;
+}
+
+template <typename R>
+void launch_recon(gks2l_ctx *c, const Par &p) {
+  const Dev &d = c->d;
+  k_recon<R><<<blocks(d.nt, TW), dim3(TW, 6), TileLayout<R>::BYTES, c->stream>>>(d, p, c->maps);
+}
+
 template <typename R>
 void launch_stage(gks2l_ctx *c, int stage) {
   const Dev &d = c->d;
   Par p = make_par(c);
-  k_recon<R><<<blocks(d.nt, 32), dim3(32, 6), 0, c->stream>>>(d, p);
+  launch_recon<R>(c, p);
   k_iface<R><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d);
   k_edge<R><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d, p, stage);
   k_update<R><<<blocks(d.nt, 128), 128, 0, c->stream>>>(d, p, stage);
@@ -424,7 +591,10 @@ void launch_stage_any(gks2l_ctx *c, int stage) {
 
 void launch_step_begin(gks2l_ctx *c) {
   Par p = make_par(c);
-  k_step_begin<<<blocks(c->d.ninst, 128), 128, 0, c->stream>>>(c->d, p, c->d_tend);
+  if (c->par.precision == GKS2L_FP32)
+    k_step_begin<float><<<blocks(c->d.ninst, 128), 128, 0, c->stream>>>(c->d, p, c->d_tend);
+  else
+    k_step_begin<double><<<blocks(c->d.ninst, 128), 128, 0, c->stream>>>(c->d, p, c->d_tend);
 }
 
 void drop_graph(gks2l_ctx *c) {
@@ -450,20 +620,25 @@ int ensure_graph(gks2l_ctx *c) {
   return 0;
 }
 
+int status_code(int st) {
+  if (st & 2) return GKS2L_ENONFINITE;
+  if (st & 1) return GKS2L_ENEGDEPTH;
+  if (st & ST_TIMEOUT) return GKS2L_ETIMEOUT;
+  return 0;
+}
+
 int check_status(gks2l_ctx *c) {
   int st = 0;
   CK(cudaMemcpyAsync(&st, c->d.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  if (st & 2) return GKS2L_ENONFINITE;
-  if (st & 1) return GKS2L_ENEGDEPTH;
-  return 0;
+  return status_code(st);
 }
 
 // Reference levels per instance: area-weighted means of h2 and eta1 = h1 + B
 // of the state in device order (host, deterministic), rounded to 2^-32.
 int set_references(gks2l_ctx *c, const double *avg_dev_order_host) {
   const Prep &P = c->prep;
-  const size_t N = P.nt;
+  const size_t N = c->cs;
   std::vector<double> ref(2 * P.ninst);
   for (int i = 0; i < P.ninst; i++) {
     double a = 0, s2 = 0, s1 = 0;
@@ -475,8 +650,8 @@ int set_references(gks2l_ctx *c, const double *avg_dev_order_host) {
     ref[2 * i] = std::ldexp(std::nearbyint(std::ldexp(s2 / a, 32)), -32);
     ref[2 * i + 1] = std::ldexp(std::nearbyint(std::ldexp(s1 / a, 32)), -32);
   }
-  CK(cudaMemcpyAsync(c->d.ref, ref.data(), ref.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  int rc;
+  if ((rc = upload(c, c->d.ref, ref)) || (rc = upload_form(c, c->d.refR, ref, 1, false))) return rc;
   return 0;
 }
 
@@ -484,7 +659,7 @@ int set_references(gks2l_ctx *c, const double *avg_dev_order_host) {
 // grad_caller (device memory, caller order, or NULL): references, mirrors,
 // reference depths on the edges, counters, CFL ratio and masses
 int after_state(gks2l_ctx *c, const double *grad_caller) {
-  const size_t N = c->prep.nt;
+  const size_t N = c->cs;
   std::vector<double> avg(6 * N);
   CK(cudaMemcpyAsync(avg.data(), c->d.avg, 6 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -492,17 +667,17 @@ int after_state(gks2l_ctx *c, const double *grad_caller) {
   if (rc) return rc;
   Par p = make_par(c);
   if (c->par.precision == GKS2L_FP32) {
-    k_mirrors<float><<<blocks(N, 128), 128, 0, c->stream>>>(c->d, c->d_perm, grad_caller);
+    k_mirrors<float><<<blocks(c->d.nt, 128), 128, 0, c->stream>>>(c->d, c->d_perm, grad_caller);
     k_edge_ref<float><<<blocks(c->d.ne, 128), 128, 0, c->stream>>>(c->d);
   } else {
-    k_mirrors<double><<<blocks(N, 128), 128, 0, c->stream>>>(c->d, c->d_perm, grad_caller);
+    k_mirrors<double><<<blocks(c->d.nt, 128), 128, 0, c->stream>>>(c->d, c->d_perm, grad_caller);
     k_edge_ref<double><<<blocks(c->d.ne, 128), 128, 0, c->stream>>>(c->d);
   }
   k_reset_stats<<<blocks(c->d.ninst, 128), 128, 0, c->stream>>>(c->d);
   CK(cudaMemsetAsync(c->d.t, 0, sizeof(double) * c->d.ninst, c->stream));
   CK(cudaMemsetAsync(c->d.dt, 0, sizeof(double) * c->d.ninst, c->stream));
   CK(cudaMemsetAsync(c->d.status, 0, sizeof(int), c->stream));
-  k_cfl<<<blocks(N, 128), 128, 0, c->stream>>>(c->d, p);
+  k_cfl<<<blocks(c->d.nt, 128), 128, 0, c->stream>>>(c->d, p);
   CK(cudaGetLastError());
   c->phase = 0;
   c->stages = 0;
@@ -580,44 +755,40 @@ int gks2l_bind(gks2l_ctx *c, void *d_workspace, size_t bytes, void *stream) {
   c->ws_bytes = bytes;
   c->stream = (cudaStream_t)stream;
   layout(c, c->ws);
+  CK(cudaMemsetAsync(c->ws, 0, need, c->stream));   // padding rows and tiles start at zero
   const Prep &P = c->prep;
-  std::vector<double> fsl(3 * P.nt), en(2 * (size_t)P.ne);
-  for (int j = 0; j < P.nt; j++)
+  const int nt = P.nt;
+  std::vector<double> fsl(3 * (size_t)nt), en(2 * (size_t)P.ne), ihs(nt), epsA(nt);
+  for (int j = 0; j < nt; j++) {
     for (int f = 0; f < 3; f++) {
-      int ce = P.cedge[f * P.nt + j];
+      int ce = P.cedge[f * nt + j];
       int e = ce >= 0 ? ce : ~ce;
-      fsl[f * P.nt + j] = (ce >= 0 ? 1.0 : -1.0) * P.elen[e] / P.area[j];
+      fsl[f * nt + j] = (ce >= 0 ? 1.0 : -1.0) * P.elen[e] / P.area[j];
     }
+    ihs[j] = 1.0 / P.hs[j];
+    epsA[j] = c->par.weno_eps * P.area[j];
+  }
   for (int e = 0; e < P.ne; e++) { en[e] = P.en0[e]; en[P.ne + e] = P.en1[e]; }
   std::vector<double> xf(4 * kMaxXf, 0.0);
   std::copy(P.xf.begin(), P.xf.end(), xf.begin());
   int rc;
   if ((rc = upload(c, c->d.inst, P.inst)) || (rc = upload(c, c->d.area, P.area)) ||
       (rc = upload(c, c->d.hs, P.hs)) || (rc = upload(c, c->d.dX, P.dX)) ||
-      (rc = upload(c, c->d.st_cell, P.st_cell)) || (rc = upload(c, c->d.st_xf, P.st_xf)) ||
-      (rc = upload(c, c->d.cedge, P.cedge)) || (rc = upload(c, c->d.fsl, fsl)) ||
+      (rc = upload_rows<int>(c, c->d.st_cell, P.st_cell, kSlots)) ||
+      (rc = upload_rows<int8_t>(c, c->d.st_xf, P.st_xf, kSlots)) ||
+      (rc = upload_rows<int>(c, c->d.cedge, P.cedge, 3)) || (rc = upload_rows<double>(c, c->d.fsl, fsl, 3)) ||
       (rc = upload(c, c->d.inst_first, P.inst_first)) || (rc = upload(c, c->d.eL, P.eL)) ||
       (rc = upload(c, c->d.eR, P.eR)) || (rc = upload(c, c->d.exf, P.exf)) || (rc = upload(c, c->d.xf, xf)) ||
-      (rc = upload(c, c->d_perm, P.perm)))
+      (rc = upload(c, c->d_perm, P.perm)) || (rc = upload_form(c, c->d.lsq, P.lsq, kCoef * kCols, true)) ||
+      (rc = upload_form(c, c->d.p1op, P.p1op, 30, true)) || (rc = upload_form(c, c->d.bq, P.bq, kBeta, true)) ||
+      (rc = upload_form(c, c->d.mmean, P.mmean, 7, true)) || (rc = upload_form(c, c->d.plane, P.plane, 6, true)) ||
+      (rc = upload_form(c, c->d.hsR, P.hs, 1, false)) || (rc = upload_form(c, c->d.ihsR, ihs, 1, false)) ||
+      (rc = upload_form(c, c->d.epsA, epsA, 1, false)) || (rc = upload_form(c, c->d.exiL, P.exiL, 1, false)) ||
+      (rc = upload_form(c, c->d.exiR, P.exiR, 1, false)) || (rc = upload_form(c, c->d.en, en, 1, false)))
     return rc;
-  if (c->rsize == 4) {
-    std::vector<float> t1, t2, t3, t4, t5, t6, t7, t8;
-    if ((rc = upload_r(c, c->d.lsq, P.lsq, t1)) || (rc = upload_r(c, c->d.p1op, P.p1op, t2)) ||
-        (rc = upload_r(c, c->d.bq, P.bq, t3)) || (rc = upload_r(c, c->d.mmean, P.mmean, t4)) ||
-        (rc = upload_r(c, c->d.exiL, P.exiL, t5)) || (rc = upload_r(c, c->d.exiR, P.exiR, t6)) ||
-        (rc = upload_r(c, c->d.plane, P.plane, t7)) || (rc = upload_r(c, c->d.en, en, t8)))
-      return rc;
-    CK(cudaStreamSynchronize(c->stream));
-  } else {
-    if ((rc = upload(c, c->d.lsq, P.lsq)) || (rc = upload(c, c->d.p1op, P.p1op)) || (rc = upload(c, c->d.bq, P.bq)) ||
-        (rc = upload(c, c->d.mmean, P.mmean)) || (rc = upload(c, c->d.exiL, P.exiL)) ||
-        (rc = upload(c, c->d.exiR, P.exiR)) || (rc = upload(c, c->d.plane, P.plane)) || (rc = upload(c, c->d.en, en)))
-      return rc;
-    CK(cudaStreamSynchronize(c->stream));
-  }
-  CK(cudaMemsetAsync(c->d.gate, 0, P.nt, c->stream));
-  CK(cudaMemsetAsync(c->d.gate_count, 0, 2 * sizeof(unsigned long long), c->stream));
-  CK(cudaMemsetAsync(c->d.status, 0, sizeof(int), c->stream));
+  if ((rc = make_maps(c))) return rc;
+  CK(cudaFuncSetAttribute(k_recon<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileLayout<float>::BYTES));
+  CK(cudaFuncSetAttribute(k_recon<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileLayout<double>::BYTES));
   c->bound = true;
   c->has_state = false;
   return upload_bathymetry(c);
@@ -638,7 +809,7 @@ int gks2l_set_state(gks2l_ctx *c, const double *avg, const double *grad) {
   const size_t nt = c->prep.nt;
   CK(cudaMemcpyAsync(c->d_stage, avg, 6 * nt * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   if (grad) CK(cudaMemcpyAsync(c->d_stage + 6 * nt, grad, 12 * nt * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  k_gather<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 6, c->d_perm, c->d_stage, c->d.avg);
+  k_gather<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, c->cs, 6, c->d_perm, c->d_stage, c->d.avg);
   CK(cudaGetLastError());
   int rc = after_state(c, grad ? c->d_stage + 6 * nt : nullptr);
   if (rc) return rc;
@@ -650,7 +821,7 @@ int gks2l_set_state_device(gks2l_ctx *c, const double *d_avg, const double *d_gr
   if (!c || !d_avg) return GKS2L_EINVAL;
   if (!c->bound) return GKS2L_ESTATE;
   const size_t nt = c->prep.nt;
-  k_gather<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 6, c->d_perm, d_avg, c->d.avg);
+  k_gather<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, c->cs, 6, c->d_perm, d_avg, c->d.avg);
   CK(cudaGetLastError());
   return after_state(c, d_grad);
 }
@@ -699,7 +870,7 @@ int gks2l_get_state(gks2l_ctx *c, double *avg, double *grad) {
   if (!c || !avg) return GKS2L_EINVAL;
   if (!c->bound || !c->has_state) return GKS2L_ESTATE;
   const size_t nt = c->prep.nt;
-  k_scatter<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 6, c->d_perm, c->d.avg, c->d_stage);
+  k_scatter<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, c->cs, 6, c->d_perm, c->d.avg, c->d_stage);
   if (c->par.precision == GKS2L_FP32)
     k_grad_out<float><<<blocks(nt, 128), 128, 0, c->stream>>>(c->d, c->d_perm, c->d_stage + 6 * nt);
   else
@@ -715,7 +886,7 @@ int gks2l_get_state_device(gks2l_ctx *c, double *d_avg, double *d_grad) {
   if (!c || !d_avg) return GKS2L_EINVAL;
   if (!c->bound || !c->has_state) return GKS2L_ESTATE;
   const size_t nt = c->prep.nt;
-  k_scatter<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, 6, c->d_perm, c->d.avg, d_avg);
+  k_scatter<<<blocks(nt, 128), 128, 0, c->stream>>>((int)nt, c->cs, 6, c->d_perm, c->d.avg, d_avg);
   if (d_grad) {
     if (c->par.precision == GKS2L_FP32)
       k_grad_out<float><<<blocks(nt, 128), 128, 0, c->stream>>>(c->d, c->d_perm, d_grad);
@@ -747,7 +918,7 @@ int gks2l_stats(gks2l_ctx *c, gks2l_stats_t *out) {
   out->t = t;
   out->dt_last = dt;
   out->stages_done = c->stages;
-  out->status = (st & 2) ? GKS2L_ENONFINITE : (st & 1) ? GKS2L_ENEGDEPTH : 0;
+  out->status = status_code(st);
   out->n_instances = c->prep.ninst;
   out->smooth_fraction = cnt[1] ? (double)cnt[0] / (double)cnt[1] : 0.0;
   return GKS2L_OK;
@@ -758,8 +929,8 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[5]) {
   if (!c->bound || !c->has_state || c->phase != 0) return GKS2L_ESTATE;
   double zero = 0.0;
   CK(cudaMemcpyAsync(c->d_tend, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  cudaEvent_t ev[10];
-  for (int i = 0; i < 10; i++) CK(cudaEventCreate(&ev[i]));
+  cudaEvent_t ev[7];
+  for (int i = 0; i < 7; i++) CK(cudaEventCreate(&ev[i]));
   double acc[5] = {0, 0, 0, 0, 0};
   const Dev &d = c->d;
   Par p = make_par(c);
@@ -770,8 +941,8 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[5]) {
     CK(cudaEventRecord(ev[1], c->stream));
     for (int stage = 1; stage <= 2; stage++) {
       CK(cudaEventRecord(ev[2], c->stream));
-      if (f32) k_recon<float><<<blocks(d.nt, 32), dim3(32, 6), 0, c->stream>>>(d, p);
-      else k_recon<double><<<blocks(d.nt, 32), dim3(32, 6), 0, c->stream>>>(d, p);
+      if (f32) launch_recon<float>(c, p);
+      else launch_recon<double>(c, p);
       CK(cudaEventRecord(ev[3], c->stream));
       if (f32) k_iface<float><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d);
       else k_iface<double><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d);
@@ -794,7 +965,7 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[5]) {
     acc[4] += t0;
   }
   CK(cudaGetLastError());
-  for (int i = 0; i < 10; i++) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 7; i++) cudaEventDestroy(ev[i]);
   for (int k = 0; k < 4; k++) ms[k] = acc[k] / (2.0 * n_steps);
   ms[4] = acc[4] / n_steps;
   c->stages += 2 * n_steps;
@@ -857,6 +1028,7 @@ const char *gks2l_error_string(int code) {
     case GKS2L_ESPACE: return "workspace too small";
     case GKS2L_ENOTIMPL: return "not implemented";
     case GKS2L_ETOOBIG: return "size beyond the fixed maximum of this entry point";
+    case GKS2L_ETIMEOUT: return "a bounded device wait gave up";
     default: return "unknown status";
   }
 }

@@ -42,9 +42,13 @@ constexpr int NCOEF = 10;    // per variable: c0 (value offset) + 9 Taylor coeff
 // Device view of the workspace. R-typed arrays are stored as void* and cast.
 struct Dev {
   int nt, ne, ninst;
+  int cs;                   // stride of per-cell arrays (nt rounded up to 32)
   // per cell
   const int *inst;
   const double *area, *hs, *dX;
+  const void *hsR, *ihsR;   // sqrt|Omega| and its inverse, type R
+  const void *epsA;         // weno_eps * |Omega|, type R
+  const void *bgR;          // [2][cell] grad B, type R
   const double *bmean, *bgx, *bgy;
   const int *st_cell;
   const int8_t *st_xf;
@@ -71,7 +75,9 @@ struct Dev {
   void *eF, *eFt, *eW, *eWt, *eWn;  // [6][edge] Gauss-point sums (weights 1/2), deviations, type R
   // per instance
   double *ref;              // [inst*2]: R2, R1
+  void *refR;               // the same, type R
   double *dt, *t;
+  void *dtR;                // dt, type R
   unsigned long long *dtbits;
   double *mass;             // [inst*2 + layer]
   int *status;
@@ -81,8 +87,14 @@ struct Dev {
 
 struct Par {
   double g, chi, cfl, eps, eps_num, gam_hi, weno_eps;
+  float gf, chif, epsf, eps_numf, gam_hif;   // the same in single precision
   int use_gate;
 };
+
+// a parameter in the form's precision
+template <typename R> __host__ __device__ __forceinline__ R pv(double d, float f);
+template <> __host__ __device__ __forceinline__ double pv<double>(double d, float) { return d; }
+template <> __host__ __device__ __forceinline__ float pv<float>(double, float f) { return f; }
 
 template <typename R> __host__ __device__ __forceinline__ R r_erf(R x);
 template <> __host__ __device__ __forceinline__ double r_erf<double>(double x) { return erf(x); }
@@ -124,7 +136,7 @@ __host__ __device__ __forceinline__ void rot2(const double *M, R v[2]) {
 // Deviation of reconstructed variable v of cell c seen through transform xf.
 template <typename R>
 __host__ __device__ __forceinline__ R img_dq(const Dev &d, int v, int c, int xf) {
-  const int N = d.nt;
+  const int N = d.cs;
   const R *dq = (const R *)d.dq;
   if (v == 0 || v == 3 || xf == 0) return dq[v * N + c];
   int b = v < 3 ? 1 : 4;
@@ -135,7 +147,7 @@ __host__ __device__ __forceinline__ R img_dq(const Dev &d, int v, int c, int xf)
 // gradient of variable v of cell c seen through transform xf
 template <typename R>
 __host__ __device__ __forceinline__ void img_dg(const Dev &d, int v, int c, int xf, R g[2]) {
-  const int N = d.nt;
+  const int N = d.cs;
   const R *G = (const R *)d.dg;
   if (xf == 0) {
     g[0] = G[(2 * v) * N + c];
@@ -165,37 +177,54 @@ __host__ __device__ __forceinline__ void img_dg(const Dev &d, int v, int c, int 
 // One cell and one variable: P3 least squares (Eq. Recons-system), three P1
 // candidates on {cell, face neighbour}, smoothness indicators and WENO-Z
 // weights, combined polynomial written as deviations in the Taylor basis.
+// Per-cell operator rows of one cell: element k of row r is at
+// base[r * stride + idx] (global arrays: stride = cell stride, idx = cell;
+// a staged shared-memory tile: stride = tile width, idx = cell in the tile).
+template <typename R> struct CellOps {
+  const R *lsq, *p1, *bq, *mm;
+  const int *st;
+  const int8_t *sx;
+  int stride, idx;
+};
+
 template <typename R>
-__host__ __device__ inline void recon_unit(const Dev &d, const Par &p, int j, int v) {
-  const int N = d.nt;
-  const R *lsq = (const R *)d.lsq;
-  const R *p1 = (const R *)d.p1op;
-  const R *bq = (const R *)d.bq;
-  const R *mm = (const R *)d.mmean;
+__host__ __device__ __forceinline__ CellOps<R> global_ops(const Dev &d, int j) {
+  CellOps<R> o;
+  o.lsq = (const R *)d.lsq; o.p1 = (const R *)d.p1op; o.bq = (const R *)d.bq; o.mm = (const R *)d.mmean;
+  o.st = d.st_cell; o.sx = d.st_xf; o.stride = d.cs; o.idx = j;
+  return o;
+}
+
+// One cell and one variable: P3 least squares (Eq. Recons-system), three P1
+// candidates on {cell, face neighbour}, smoothness indicators and WENO-Z
+// weights, combined polynomial written as deviations in the Taylor basis.
+template <typename R>
+__host__ __device__ inline void recon_unit(const Dev &d, const Par &p, const CellOps<R> &o, int j, int v) {
+  const int N = d.cs, S = o.stride, I = o.idx;
   R *coef = (R *)d.coef;
   const R q0 = ((const R *)d.dq)[v * N + j];
-  const R hs = (R)d.hs[j];
+  const R hs = ((const R *)d.hsR)[j];
   R rhs[NCOL];
   for (int s = 0; s < NSLOT; s++) {
-    int c = d.st_cell[s * N + j];
-    rhs[s] = c >= 0 ? img_dq<R>(d, v, c, d.st_xf[s * N + j]) - q0 : (R)0;
+    int c = o.st[s * S + I];
+    rhs[s] = c >= 0 ? img_dq<R>(d, v, c, o.sx[s * S + I]) - q0 : (R)0;
   }
   R g[2];
   img_dg<R>(d, v, j, 0, g);
   rhs[9] = hs * g[0];
   rhs[10] = hs * g[1];
   for (int f = 0; f < 3; f++) {
-    img_dg<R>(d, v, d.st_cell[f * N + j], d.st_xf[f * N + j], g);
+    img_dg<R>(d, v, o.st[f * S + I], o.sx[f * S + I], g);
     rhs[11 + 2 * f] = hs * g[0];
     rhs[12 + 2 * f] = hs * g[1];
   }
   R a[9];
   for (int r = 0; r < 9; r++) {
     R s = 0;
-    for (int c = 0; c < NCOL; c++) s += lsq[(r * NCOL + c) * N + j] * rhs[c];
+    for (int c = 0; c < NCOL; c++) s += o.lsq[(r * NCOL + c) * S + I] * rhs[c];
     a[r] = s;
   }
-  const R gh = (R)p.gam_hi, gl = (R)((1.0 - p.gam_hi) / 3.0);
+  const R gh = pv<R>(p.gam_hi, p.gam_hif), gl = ((R)1 - gh) * (R)(1.0 / 3.0);
   R fac = 1, wf[3] = {gl, gl, gl}, b[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   const bool linear = p.use_gate && d.gate[j];
   if (!linear) {
@@ -204,7 +233,7 @@ __host__ __device__ inline void recon_unit(const Dev &d, const Par &p, int j, in
       R r5[5] = {rhs[f], rhs[9], rhs[10], rhs[11 + 2 * f], rhs[12 + 2 * f]};
       for (int k = 0; k < 2; k++) {
         R s = 0;
-        for (int c = 0; c < 5; c++) s += p1[((f * 2 + k) * 5 + c) * N + j] * r5[c];
+        for (int c = 0; c < 5; c++) s += o.p1[((f * 2 + k) * 5 + c) * S + I] * r5[c];
         b[f][k] = s;
       }
       beta[1 + f] = b[f][0] * b[f][0] + b[f][1] * b[f][1];
@@ -212,14 +241,15 @@ __host__ __device__ inline void recon_unit(const Dev &d, const Par &p, int j, in
     R bh = 0;
     int idx = 0;
     for (int k = 0; k < 9; k++)
-      for (int l = k; l < 9; l++) bh += bq[(idx++) * N + j] * a[k] * a[l];
+      for (int l = k; l < 9; l++) bh += o.bq[(idx++) * S + I] * a[k] * a[l];
     beta[0] = bh;
     R tz = (r_abs<R>(bh - beta[1]) + r_abs<R>(bh - beta[2]) + r_abs<R>(bh - beta[3])) * (R)(1.0 / 3.0);
     // the variable's value (reference + deviation) scales the regulariser
     R Q0 = q0;
-    if (v == 0) Q0 += (R)d.ref[2 * d.inst[j]];
-    if (v == 3) Q0 += (R)d.ref[2 * d.inst[j] + 1];
-    R eps = (R)(p.weno_eps * d.area[j]) * (1 + Q0 * Q0);
+    const R *refR = (const R *)d.refR;
+    if (v == 0) Q0 += refR[2 * d.inst[j]];
+    if (v == 3) Q0 += refR[2 * d.inst[j] + 1];
+    R eps = ((const R *)d.epsA)[j] * (1 + Q0 * Q0);
     R w[4], ws = 0;
     const R gam[4] = {gh, gl, gl, gl};
     for (int k = 0; k < 4; k++) {
@@ -240,7 +270,7 @@ __host__ __device__ inline void recon_unit(const Dev &d, const Par &p, int j, in
     r[2] += cf * b[f][1];
   }
   R c0 = 0;
-  for (int k = 3; k < 10; k++) c0 -= r[k] * mm[(k - 3) * N + j];
+  for (int k = 3; k < 10; k++) c0 -= r[k] * o.mm[(k - 3) * S + I];
   r[0] = c0;
   for (int k = 0; k < 10; k++) coef[(v * NCOEF + k) * N + j] = r[k];
   if (v == 3) ((R *)d.omg)[j] = fac;
@@ -264,13 +294,13 @@ template <typename R> struct SideVals {
 // href is the depth of the reference level at the point
 template <typename R>
 __host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, R x, R y, R href, SideVals<R> &s) {
-  const int N = d.nt;
+  const int N = d.cs;
   const R *coef = (const R *)d.coef;
   const R *dq = (const R *)d.dq;
   const int v0 = ell == 0 ? 3 : 0, vo = ell == 0 ? 0 : 3;
   R m[10], mx[10], my[10];
   monos<R>(x, y, m, mx, my);
-  const R ih = (R)(1.0 / d.hs[c]);
+  const R ih = ((const R *)d.ihsR)[c];
   R dev[3], gx[4], gy[4];
   for (int i = 0; i < 4; i++) {
     int v = i < 3 ? v0 + i : vo;
@@ -294,7 +324,7 @@ __host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, 
   s.gm[1][0] = gx[2]; s.gm[1][1] = gy[2];
   s.goth[0] = gx[3]; s.goth[1] = gy[3];
   R gb[2] = {0, 0};
-  if (ell == 0) { gb[0] = (R)d.bgx[c]; gb[1] = (R)d.bgy[c]; }
+  if (ell == 0) { gb[0] = ((const R *)d.bgR)[c]; gb[1] = ((const R *)d.bgR)[N + c]; }
   if (xf != 0) {
     const double *M = d.xf + 4 * xf;
     R mv[2] = {s.mx, s.my};
@@ -320,7 +350,7 @@ __host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, 
 template <typename R>
 __host__ __device__ __forceinline__ R ref_depth(const Dev &d, int ell, int e, int q) {
   if (ell == 0) return ((const R *)d.hrefe)[q * d.ne + e];
-  return (R)d.ref[2 * d.inst[d.eL[e]]];
+  return ((const R *)d.refR)[2 * d.inst[d.eL[e]]];
 }
 
 // ------------------------------------------------ gas-kinetic interface solution
@@ -519,7 +549,7 @@ __host__ __device__ inline R iface_unit(const Dev &d, int e, int ell, int q) {
 // plane gradient (Sec. 2.3) of the blended level `which` for cell c
 template <typename R>
 __host__ __device__ __forceinline__ void plane_grad(const Dev &d, int c, int which, R g[2]) {
-  const int N = d.nt, NE = d.ne;
+  const int N = d.cs, NE = d.ne;
   const R *pl = (const R *)d.plane, *hc = (const R *)d.hc;
   g[0] = g[1] = 0;
   for (int f = 0; f < 3; f++) {
@@ -539,7 +569,7 @@ __host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int
   const int NE = d.ne;
   const R *xl = (const R *)d.exiL, *xr = (const R *)d.exiR, *en = (const R *)d.en;
   int cL = d.eL[e], cR = d.eR[e], xf = d.exf[e];
-  const R dt = (R)d.dt[d.inst[cL]];
+  const R dt = ((const R *)d.dtR)[d.inst[cL]];
   const R delta = stage == 1 ? dt : (R)0.5 * dt;
   const R href = ref_depth<R>(d, ell, e, q);
   SideVals<R> s[2];
@@ -549,13 +579,13 @@ __host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int
   // D = grad h - grad Phi / G = grad(level) + c (w grad(other) + (1 - w) grad P1)
   const int oth = 1 - ell;  // hc / omg index of the other layer: 0 = eta1, 1 = h2
   const R *om = (const R *)d.omg;
-  R w = om[oth * d.nt + cL] < om[oth * d.nt + cR] ? om[oth * d.nt + cL] : om[oth * d.nt + cR];
+  R w = om[oth * d.cs + cL] < om[oth * d.cs + cR] ? om[oth * d.cs + cL] : om[oth * d.cs + cR];
   w = w < (R)0 ? (R)0 : (w > (R)1 ? (R)1 : w);
   R pl[2][2];
   plane_grad<R>(d, cL, oth, pl[0]);
   plane_grad<R>(d, cR, oth, pl[1]);
   if (xf != 0) rot2<R>(d.xf + 4 * xf, pl[1]);
-  const R cf = (R)(ell == 0 ? p.chi : 1.0);
+  const R cf = ell == 0 ? pv<R>(p.chi, p.chif) : (R)1;
   const R n0 = en[e], n1 = en[NE + e];
   R U[2], V[2], dn[2][3], dtt[2][3], D[2][2];
   for (int sd = 0; sd < 2; sd++) {
@@ -583,10 +613,10 @@ __host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int
   // collision time (Sec. 4): tau = eps dt + eps_num |(hl^2 - hr^2)/(hl^2 + hr^2)| dt
   const R hl = s[0].h, hr = s[1].h;
   const R jump = r_abs<R>((s[0].d - s[1].d) * (hl + hr) / (hl * hl + hr * hr));
-  const R tau = (R)p.eps * dt + (R)p.eps_num * jump * dt;
+  const R tau = pv<R>(p.eps, p.epsf) * dt + pv<R>(p.eps_num, p.eps_numf) * jump * dt;
   R F[3], Ft[3], W[3], Wt[3];
-  gks_layer<R>(href, s[0].d, s[1].d, U[0], V[0], U[1], V[1], dn[0], dtt[0], D[0], dn[1], dtt[1], D[1], (R)p.g,
-               tau, delta, F, Ft, W, Wt);
+  gks_layer<R>(href, s[0].d, s[1].d, U[0], V[0], U[1], V[1], dn[0], dtt[0], D[0], dn[1], dtt[1], D[1],
+               pv<R>(p.g, p.gf), tau, delta, F, Ft, W, Wt);
   const R *src[4] = {F, Ft, W, Wt};
   for (int k = 0; k < 4; k++) {
     out[3 * k] = src[k][0];
@@ -601,14 +631,15 @@ __host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int
 // Returns the CFL ratio dX/U_max of the new state (stage 2) or 0.
 template <typename R>
 __host__ __device__ inline double update_unit(const Dev &d, const Par &p, int j, int stage, int *flags) {
-  const int N = d.nt, NE = d.ne;
+  const int N = d.cs, NE = d.ne;
   const int in = d.inst[j];
   const double dt = d.dt[in];
   if (!(dt > 0)) return 0;
   const R *eF = (const R *)d.eF, *eFt = (const R *)d.eFt, *eWt = (const R *)d.eWt, *eWn = (const R *)d.eWn;
   const R *Wcur = stage == 1 ? eWn : (const R *)d.eW;
   const R *en = (const R *)d.en;
-  const R cend = (R)(stage == 1 ? 0.5 * dt : dt);
+  const R dtr = ((const R *)d.dtR)[in];
+  const R cend = stage == 1 ? (R)0.5 * dtr : dtr;
   // mass residuals in FP64 (exact conservation), the rest in R
   double LFm[2] = {0, 0}, LFtm[2] = {0, 0};
   R LF[NV] = {0}, LFt[NV] = {0}, mW[NV] = {0}, mWt[NV] = {0};
@@ -638,10 +669,10 @@ __host__ __device__ inline double update_unit(const Dev &d, const Par &p, int j,
       GGn[v][0] += snx * We; GGn[v][1] += sny * We;
     }
   }
-  const R G = (R)p.g, chi = (R)p.chi;
-  const R gb[2] = {(R)d.bgx[j], (R)d.bgy[j]};
+  const R G = pv<R>(p.g, p.gf), chi = pv<R>(p.chi, p.chif);
+  const R gb[2] = {((const R *)d.bgR)[j], ((const R *)d.bgR)[N + j]};
   const R *dq = (const R *)d.dq;
-  const R R2 = (R)d.ref[2 * in];
+  const R R2 = ((const R *)d.refR)[2 * in];
   const R hrc = ((const R *)d.hrefc)[j];          // R1 - B_j
   const R m1 = hrc + mW[3], m2 = R2 + mW[0];       // means of h1, h2 over the 6 Gauss points
   const R LFh2 = (R)LFm[0], LFh1 = (R)LFm[1];

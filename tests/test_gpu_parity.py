@@ -108,7 +108,9 @@ def test_odd_stage_counts_and_restart_are_exact():
     s2.advance(4)
     a2, g2 = s2.get_state()
     assert np.array_equal(a1, a2) and np.array_equal(g1, g2)
-    # checkpoint/restart: 6 + 6 stages == 12 stages
+    # checkpoint/restart: 6 + 6 stages == 12 stages to rounding (the state's
+    # grad h1 is stored as grad eta1 = grad h1 + grad B, so the round trip
+    # through the ABI costs one rounding)
     s2.advance(8)
     a12, g12 = s2.get_state()
     s3 = g.problem_solver(prob)
@@ -118,7 +120,8 @@ def test_odd_stage_counts_and_restart_are_exact():
     s4.set_state(ca, cg)
     s4.advance(6)
     b12, h12 = s4.get_state()
-    assert np.array_equal(a12, b12) and np.array_equal(g12, h12)
+    ra, rg = max_rel(prob, b12, h12, a12, g12)
+    assert ra <= 1e-13 and rg <= 1e-12, (ra, rg)
 
 
 @pytest.mark.parametrize("precision", [FP64, FP32])
