@@ -158,17 +158,56 @@ int gks2l_get_state_device(gks2l_ctx *ctx, double *d_avg, double *d_grad);
 /* Mass sums, time, step and device status; synchronises the stream. */
 int gks2l_stats(gks2l_ctx *ctx, gks2l_stats_t *out);
 
-/* Load the troubled-cell gate: 24->32->32->1 MLP, weights as float32
- * [W1 (32x24), b1 (32), W2 (32x32), b2 (32), W3 (1x32), b3 (1)] and input
- * normalisation [mean (24), inv_std (24)]; stored on the device in bf16
- * (weights) and fp32 (biases, normalisation). */
+/* ---- learned troubled-cell gate (not part of the paper) ------------------
+ * A 24 -> 32 -> 32 -> 1 MLP (ReLU hidden layers, sigmoid output) predicts per
+ * cell whether the nonlinear WENO weights of the reconstruction would depart
+ * from the linear ones; cells it calls smooth take the linear P3
+ * reconstruction and a blending weight w = 1. The network runs inside each
+ * reconstruction and its decisions apply to the next one (the first stage
+ * after gks2l_set_state or gks2l_set_mlp is the plain method). Parameters are a float vector
+ * of GKS2L_MLP_NPARAM entries:
+ *   W1[32][24], b1[32], W2[32][32], b2[32], w3[32], b3, mean[24], inv_std[24]
+ * (the first GKS2L_MLP_NTRAIN are trained; features are (x - mean) * inv_std).
+ * Weights run as BF16 on the tensor cores with FP32 accumulation. */
+#define GKS2L_MLP_NPARAM 1937
+#define GKS2L_MLP_NTRAIN 1889
+
+/* Load the gate into a bound context (host params); it acts when the
+ * context was created with indicator = GKS2L_INDICATOR_MLP. */
 int gks2l_set_mlp(gks2l_ctx *ctx, const float *params, size_t n_floats);
 
-/* Per-cell training data for the gate from the current state (device
- * arrays, caller order): features[24 * n_tri] (normalised inputs, raw) and
- * labels[n_tri] = 1 where the nonlinear weights of eta1 or h2 depart from the
- * linear ones by more than `tol` (max |omega_k/gamma_k - 1|). */
-int gks2l_harvest(gks2l_ctx *ctx, float tol, float *d_features, float *d_labels);
+/* Training data from the current state (after any number of stages), in the
+ * caller's cell order: 24 features per cell d_features[24 * n_tri] and the
+ * label d_labels[n_tri] = 1 where, in the plain nonlinear reconstruction of
+ * the current state, max over the six variables and four WENO weights of
+ * |omega_k / gamma_k - 1| exceeds tol. Features, columns 0-11 for eta1 and
+ * 12-23 for h2: over the cell and its three face neighbours (face k is the
+ * edge from vertex k to vertex k+1), the deviation of the average from the
+ * four-cell mean and sqrt(|Omega|) times the gradient, divided by
+ * sqrt(sum of their squares + weno_eps |Omega| (1 + q0^2)). d_logits: null,
+ * or n_tri floats for the logits the fused gate computes for these cells
+ * (needs a network loaded by gks2l_set_mlp). All pointers are device memory.
+ * Synchronises the stream; the state is not changed (a gate loaded with
+ * gks2l_set_mlp takes its decisions for the next stage from this state). */
+int gks2l_harvest(gks2l_ctx *ctx, float tol, float *d_features, float *d_labels, float *d_logits);
+
+/* Gradient of the weighted logistic loss
+ *   L = sum_i pos_weight y_i softplus(-s_i) + (1 - y_i) softplus(s_i)
+ * of n samples (device d_X[n][24], d_y[n] in {0, 1}) for parameters d_params
+ * (device, GKS2L_MLP_NPARAM floats): writes d_grads[GKS2L_MLP_NTRAIN] (sums
+ * over the samples) and d_loss[1]. BF16 tensor cores, FP32 sums. */
+int gks2l_mlp_grad(const float *d_X, const float *d_y, int32_t n, const float *d_params, float pos_weight,
+                   float *d_grads, float *d_loss, void *stream);
+
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) on the trained parameters with
+ * gradients scaled by `scale`; step counts from 1. d_m, d_v: moment buffers of
+ * GKS2L_MLP_NTRAIN floats, zero before the first step. */
+int gks2l_mlp_adam(float *d_params, const float *d_grads, float *d_m, float *d_v, int32_t step, float lr,
+                   float scale, void *stream);
+
+/* Logits of n samples (device d_X[n][24]) with the tensor-core inference
+ * path the reconstruction uses. */
+int gks2l_mlp_forward(const float *d_X, int32_t n, const float *d_params, float *d_logits, void *stream);
 
 /* Kernel timing for roofline reports: advances n_steps full steps (exactly
  * like gks2l_advance, state included) but launches the stage kernels one by

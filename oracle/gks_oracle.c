@@ -166,6 +166,8 @@ typedef struct {
   /* stage work arrays */
   double *coef;                          /* NB per (cell,var): reconstructed polynomial */
   double *omegaH;                        /* per (cell,var): nonlinear weight of the P3 candidate */
+  double *wdev;                          /* per (cell,var): max_k |omega_k / gamma_k - 1|        */
+  unsigned char *linear;                 /* per cell: 1 = take the linear weights (gate), or NULL */
   double *hc;                            /* per edge: edge-centre blended heights, layer 1 (depth), layer 2 */
   double *plane;                         /* per cell: grad of the P1 plane of h1_hat (2) and h2_hat (2) */
   double *eF, *eFt, *eW, *eWt;           /* per edge per Gauss point: 6 each, global frame */
@@ -633,6 +635,15 @@ static void reconstruct(orc_t *o) {
         ws += w[k];
       }
       for (int k = 0; k < 4; k++) w[k] /= ws;
+      double dev = 0;
+      for (int k = 0; k < 4; k++) dev = fmax(dev, fabs(w[k] / gam[k] - 1));
+      o->wdev[j * NVAR + v] = dev;
+      if (o->linear && o->linear[j]) {
+        /* a cell the troubled-cell gate calls smooth: linear weights, so the */
+        /* combination is the P3 polynomial itself (and the blend w is 1)     */
+        for (int k = 0; k < 4; k++) w[k] = gam[k];
+        o->wdev[j * NVAR + v] = 0;
+      }
       /* R = (w_H/g_H) (P3 - sum g_m P1_m) + sum w_m P1_m, in the zero-mean basis */
       double *cf = &o->coef[(j * NVAR + v) * NB];
       double fac = w[0] / gh;
@@ -1196,6 +1207,7 @@ orc_t *orc_create(int nv, const double *xy, int nt, const int *tri, const signed
   o->grad = calloc(2 * NVAR * nt, sizeof(double));
   o->coef = calloc(NB * NVAR * nt, sizeof(double));
   o->omegaH = calloc(NVAR * nt, sizeof(double));
+  o->wdev = calloc(NVAR * nt, sizeof(double));
   o->hc = calloc(2 * ne, sizeof(double));
   o->plane = calloc(4 * nt, sizeof(double));
   o->eF = calloc(2 * NVAR * ne, sizeof(double)); o->eFt = calloc(2 * NVAR * ne, sizeof(double));
@@ -1211,7 +1223,7 @@ void orc_destroy(orc_t *o) {
   void *ptrs[] = {o->xy, o->tri, o->tri_bc, o->bvert, o->area, o->cx, o->cy, o->hs, o->dX, o->bmean,
                   o->bgrad, o->mean_m, o->face, o->face_edge, o->face_side, o->navg, o->avg_img, o->M,
                   o->N1, o->edge, o->avg, o->grad, o->coef, o->omegaH, o->hc, o->plane, o->eF, o->eFt,
-                  o->eW, o->eWt, o->eWn, o->Wn, o->Ln, o->Ltn};
+                  o->eW, o->eWt, o->eWn, o->Wn, o->Ln, o->Ltn, o->wdev, o->linear};
   for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); i++) free(ptrs[i]);
   free(o);
 }
@@ -1286,6 +1298,53 @@ void orc_eval(const orc_t *o, int c, double x, double y, double *val6, double *g
   for (int k = 0; k < NVAR; k++) { val6[k] = v[k]; grad12[2 * k] = g[k][0]; grad12[2 * k + 1] = g[k][1]; }
 }
 void orc_omega(const orc_t *o, double *om /* nt*6 */) { memcpy(om, o->omegaH, sizeof(double) * o->nt * NVAR); }
+
+/* ---- troubled-cell gate (an addition to the paper's scheme) -------------- */
+/* Largest departure of the four WENO weights from the linear ones, per      */
+/* (cell, variable), from the last reconstruction.                           */
+void orc_weight_departure(const orc_t *o, double *out /* nt*6 */) {
+  memcpy(out, o->wdev, sizeof(double) * o->nt * NVAR);
+}
+/* Cells with mask[j] = 1 take the linear weights in every later            */
+/* reconstruction; NULL removes the mask.                                    */
+void orc_set_linear_mask(orc_t *o, const unsigned char *mask) {
+  free(o->linear);
+  o->linear = NULL;
+  if (mask) {
+    o->linear = malloc(o->nt);
+    memcpy(o->linear, mask, o->nt);
+  }
+}
+/* Gate inputs of every cell at the current state: for eta1 (columns 0-11)   */
+/* and h2 (columns 12-23), over the cell and its three face neighbours       */
+/* (face k is the edge from vertex k to vertex k+1), the deviation of the    */
+/* average from the mean of the four and the size-scaled gradient hs * grad, */
+/* all divided by sqrt(sum of their squares + weno_eps |Omega| (1 + q0^2)).  */
+void orc_gate_features(const orc_t *o, double *X /* nt*24 */) {
+  const int var[2] = {3, 0};
+  for (int j = 0; j < o->nt; j++) {
+    image_t self = {j, aff_id()};
+    double q[4][NVAR], g[4][NVAR][2];
+    image_avg(o, &self, q[0]);
+    image_grad(o, &self, g[0]);
+    for (int f = 0; f < 3; f++) {
+      image_avg(o, &o->face[IDX2(j, f)], q[1 + f]);
+      image_grad(o, &o->face[IDX2(j, f)], g[1 + f]);
+    }
+    for (int s = 0; s < 2; s++) {
+      int v = var[s];
+      double mean = (q[0][v] + q[1][v] + q[2][v] + q[3][v]) / 4, raw[12], ss = 0;
+      for (int m = 0; m < 4; m++) {
+        raw[3 * m] = q[m][v] - mean;
+        raw[3 * m + 1] = o->hs[j] * g[m][v][0];
+        raw[3 * m + 2] = o->hs[j] * g[m][v][1];
+      }
+      for (int k = 0; k < 12; k++) ss += raw[k] * raw[k];
+      ss += o->weno_eps * o->area[j] * (1 + q[0][v] * q[0][v]);
+      for (int k = 0; k < 12; k++) X[j * 24 + 12 * s + k] = raw[k] / sqrt(ss);
+    }
+  }
+}
 int orc_stencil_size(const orc_t *o, int c) { return o->navg[c]; }
 
 /* Gauss points of every edge (L's frame) and the Gauss-theorem gradient of  */

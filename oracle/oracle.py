@@ -60,6 +60,9 @@ def lib():
         _lib.orc_reconstruct.argtypes = [p]
         _lib.orc_eval.argtypes = [p, i, d, d, p, p]
         _lib.orc_omega.argtypes = [p, p]
+        _lib.orc_weight_departure.argtypes = [p, p]
+        _lib.orc_set_linear_mask.argtypes = [p, p]
+        _lib.orc_gate_features.argtypes = [p, p]
         _lib.orc_stencil_size.argtypes = [p, i]
         _lib.orc_edge_points.argtypes = [p, p, p]
         _lib.orc_gauss_gradient.argtypes = [p, p, p]
@@ -160,6 +163,27 @@ class Oracle:
         om = np.zeros(self.nt * 6)
         lib().orc_omega(self._h, _ptr(om))
         return om.reshape(self.nt, 6)
+
+    def weight_departure(self):
+        """max_k |omega_k / gamma_k - 1| per (cell, variable) of the last reconstruction."""
+        out = np.zeros(self.nt * 6)
+        lib().orc_weight_departure(self._h, _ptr(out))
+        return out.reshape(self.nt, 6)
+
+    def set_linear_mask(self, mask):
+        """Cells with mask = 1 take the linear weights from now on (None: none)."""
+        if mask is None:
+            lib().orc_set_linear_mask(self._h, None)
+            return
+        self._mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        assert self._mask.shape == (self.nt,)
+        lib().orc_set_linear_mask(self._h, _ptr(self._mask))
+
+    def gate_features(self):
+        """The 24 troubled-cell gate inputs of every cell at the current state."""
+        X = np.zeros(self.nt * 24)
+        lib().orc_gate_features(self._h, _ptr(X))
+        return X.reshape(self.nt, 24)
 
     def stencil_size(self, c):
         return lib().orc_stencil_size(self._h, int(c))

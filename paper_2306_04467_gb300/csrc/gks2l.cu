@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "gks2l.h"
+#include "mlp.cuh"
 #include "prep.h"
 #include "stage.cuh"
 
@@ -34,6 +35,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr unsigned long long DBL_INF_BITS = 0x7FF0000000000000ull;
 constexpr int TW = 32;                  // cells per reconstruction tile
 constexpr int ST_TIMEOUT = 4;           // status bit: a bounded wait gave up
+constexpr int GATE_LD = 40;             // padded row stride of the gate feature tile (bank spread)
 
 // ---------------------------------------------------------------- TMA staging
 // Operator rows of one tile of TW cells in shared memory, [row][TW] each.
@@ -49,8 +51,10 @@ template <typename R> struct TileLayout {
   static constexpr unsigned ST = MM + 7 * TW * sizeof(R);
   static constexpr unsigned SX = ST + kSlots * TW * 4;
   static constexpr unsigned BAR = SX + 384;                   // 9 * 32 int8 rounded to 128 B
-  static constexpr unsigned BYTES = BAR + 16;
+  static constexpr unsigned XT = BAR + 128;                   // gate features, [32][GATE_LD] bf16
+  static constexpr unsigned BYTES = XT + 32 * GATE_LD * 2;
   static constexpr unsigned TX = BAR - 96;                    // bytes the six copies deliver
+  static constexpr unsigned TX_LINEAR = TX - (MM - P1);       // without the P1 and beta rows
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -90,35 +94,48 @@ __device__ __forceinline__ bool mbar_wait_bounded(void *bar, unsigned long long 
 }
 
 // ------------------------------------------------------------------ kernels
+// resident reconstruction blocks per SM the register budget is held to
+template <typename R> struct ReconOcc { static constexpr int value = 6; };
+template <> struct ReconOcc<double> { static constexpr int value = 4; };
+
 template <typename R>
-__global__ void __launch_bounds__(192) k_recon(Dev d, Par p, const __grid_constant__ ReconMaps maps) {
+__global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p, const __grid_constant__ ReconMaps maps) {
   using T = TileLayout<R>;
   extern __shared__ __align__(128) unsigned char sm[];
   const int j0 = blockIdx.x * TW;
   void *bar = sm + T::BAR;
+  // troubled-cell gate: the previous reconstruction left the mask of this
+  // tile's cells it calls smooth; a tile whose cells all take the linear
+  // weights needs neither the P1 rows nor the smoothness forms
+  const bool gate_on = p.use_gate && !p.harvest;
+  const unsigned lin_mask = gate_on ? d.gate_mask[blockIdx.x] : 0u;
+  const bool all_linear = lin_mask == 0xffffffffu;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(T::TX)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(all_linear ? T::TX_LINEAR : T::TX)
                  : "memory");
     tma_load_2d(sm + T::LSQ, &maps.lsq, j0, 0, bar);
-    tma_load_2d(sm + T::P1, &maps.p1, j0, 0, bar);
-    tma_load_2d(sm + T::BQ, &maps.bq, j0, 0, bar);
+    if (!all_linear) {
+      tma_load_2d(sm + T::P1, &maps.p1, j0, 0, bar);
+      tma_load_2d(sm + T::BQ, &maps.bq, j0, 0, bar);
+    }
     tma_load_2d(sm + T::MM, &maps.mm, j0, 0, bar);
     tma_load_2d(sm + T::ST, &maps.st, j0, 0, bar);
     tma_load_2d(sm + T::SX, &maps.sx, j0, 0, bar);
   }
   __syncthreads();
-  if (!mbar_wait_bounded(bar, 1000000000ull)) {
+  const bool landed = mbar_wait_bounded(bar, 1000000000ull);
+  if (!__syncthreads_and(landed)) {
     // the copies did not land within a second: report, wait for them once
-    // more (bounded) so no copy outlives the block, and leave
+    // more (bounded) so no copy outlives the block, and leave (all threads)
     if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(d.status, ST_TIMEOUT);
-    mbar_wait_bounded(bar, 1000000000ull);
+    if (!landed) mbar_wait_bounded(bar, 1000000000ull);
     return;
   }
-  const int j = j0 + threadIdx.x;
-  if (j >= d.nt) return;
-  if (!(d.dt[d.inst[j]] > 0)) return;
+  const int j = j0 + threadIdx.x, v = threadIdx.y;
+  const bool active = j < d.nt && (p.all_active || d.dt[d.inst[j]] > 0);
   CellOps<R> o;
   o.lsq = (const R *)(sm + T::LSQ);
   o.p1 = (const R *)(sm + T::P1);
@@ -128,7 +145,73 @@ __global__ void __launch_bounds__(192) k_recon(Dev d, Par p, const __grid_consta
   o.sx = (const int8_t *)(sm + T::SX);
   o.stride = TW;
   o.idx = threadIdx.x;
-  recon_unit<R>(d, p, o, j, threadIdx.y);
+  const bool linear = ((lin_mask >> threadIdx.x) & 1u) != 0;
+  if (gate_on && v == 0) {
+    const unsigned ns = __popc(__ballot_sync(FULL, active && linear)), nc = __popc(__ballot_sync(FULL, active));
+    if (threadIdx.x == 0) {
+      atomicAdd(&d.gate_count[0], (unsigned long long)ns);
+      atomicAdd(&d.gate_count[1], (unsigned long long)nc);
+    }
+  }
+  R rhs[NCOL], a[9];
+  if (active) {
+    recon_gather<R>(d, o, j, v, rhs);
+    recon_p3<R>(o, rhs, a);
+    recon_finish<R>(d, p, o, j, v, rhs, a, linear);
+  }
+  if (!p.use_gate || (v != 0 && v != 3)) return;
+  // The gate for the next reconstruction of these cells: the h2 and eta1
+  // warps turn their right-hand sides into the 24 features, meet at a named
+  // barrier, and each runs the network on the tensor cores for 16 cells
+  // (weights read through L1); each writes its half of the tile's mask.
+  const MlpDev &w = *reinterpret_cast<const MlpDev *>(d.mlp);
+  __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(sm + T::XT);
+  unsigned *row = reinterpret_cast<unsigned *>(X + threadIdx.x * GATE_LD);
+  {
+    float f[12];
+    if (active) {
+      gate_features_rhs<R>(d, j, v, rhs, f);
+    } else {
+      for (int k = 0; k < 12; k++) f[k] = 0.f;
+    }
+    // the image has the normalisation folded into the first layer
+    const int off = v == 3 ? 0 : 6;
+    for (int k = 0; k < 6; k++) row[off + k] = pack_bf16(f[2 * k], f[2 * k + 1]);
+    if (v == 0)
+      for (int k = 12; k < 16; k++) row[k] = 0u;   // columns 24..31
+  }
+  asm volatile("bar.sync 1, 64;" ::: "memory");
+  const int lane = threadIdx.x, mt = v == 0 ? 0 : 1, r = 16 * mt + (lane & 15), jr = j0 + r;
+  const float logit = mlp_rows16(w, X, GATE_LD, mt, lane);
+  const bool row_active = jr < d.nt && (p.all_active || d.dt[d.inst[jr]] > 0);
+  const bool smooth = lane < 16 && row_active && logit < w.threshold;
+  const unsigned bits = __ballot_sync(FULL, smooth || (lane < 16 && !row_active)) & 0xffffu;
+  if (lane == 0) reinterpret_cast<unsigned short *>(d.gate_mask)[2 * blockIdx.x + mt] = (unsigned short)bits;
+  if (lane < 16 && p.logit_out && jr < d.nt) p.logit_out[jr] = logit;
+}
+
+// gate network image for the reconstruction blocks (one block)
+__global__ void k_mlp_pack(const float *P, float threshold_logit, MlpDev *out) {
+  mlp_pack_folded(*out, P, threshold_logit, threadIdx.x, blockDim.x);
+}
+
+// training data for the gate, written in the caller's cell order: 24
+// features, the label (largest departure of the WENO weights from the linear
+// ones over the six variables above tol) and, if asked, the gate logits the
+// reconstruction computed
+template <typename R>
+__global__ void k_harvest(Dev d, const int *perm, float tol, const float *logit_dev, float *X, float *y,
+                          float *logits) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.nt) return;
+  const size_t c = (size_t)perm[j];
+  float f[24];
+  gate_features<R>(d, j, d.st_cell, d.st_xf, d.cs, j, f);
+  for (int k = 0; k < 24; k++) X[c * 24 + k] = f[k];
+  float dv = 0.f;
+  for (int v = 0; v < NV; v++) dv = fmaxf(dv, d.wdev[v * d.cs + j]);
+  y[c] = dv > tol ? 1.f : 0.f;
+  if (logits) logits[c] = logit_dev[j];
 }
 
 template <typename R>
@@ -389,6 +472,8 @@ struct gks2l_ctx {
   double *d_tend = nullptr;
   double *d_stage = nullptr;   // 18 * nt staging for permutations
   std::vector<double> bmean_h; // cell-average bottom (device order), host copy
+  bool has_mlp = false;
+  int n_sm = 1;                // SMs of the bound device
   int phase = 0;
   int64_t stages = 0;
   cudaGraph_t graph = nullptr;
@@ -436,7 +521,9 @@ size_t layout(gks2l_ctx *c, char *base) {
   d.Ltn = k.take<double>(6 * cs);
   d.coef = k.take<char>(rs * 60 * cs);
   d.omg = k.take<char>(rs * 2 * cs);
-  d.gate = k.take<uint8_t>(nt);
+  d.mlp = k.take<MlpDev>(1);
+  d.gate_mask = k.take<unsigned>(cs / TW);
+  d.wdev = k.take<float>(6 * cs);
   d.eL = k.take<int>(ne);
   d.eR = k.take<int>(ne);
   d.exf = k.take<int8_t>(ne);
@@ -522,7 +609,10 @@ Par make_par(const gks2l_ctx *c) {
   p.gam_hi = c->par.weno_gamma_hi; p.weno_eps = c->par.weno_eps;
   p.gf = (float)p.g; p.chif = (float)p.chi; p.epsf = (float)p.eps; p.eps_numf = (float)p.eps_num;
   p.gam_hif = (float)p.gam_hi;
-  p.use_gate = c->par.indicator == GKS2L_INDICATOR_MLP ? 1 : 0;
+  p.use_gate = (c->par.indicator == GKS2L_INDICATOR_MLP && c->has_mlp) ? 1 : 0;
+  p.harvest = 0;
+  p.logit_out = nullptr;
+  p.all_active = 0;
   return p;
 }
 
@@ -677,6 +767,9 @@ int after_state(gks2l_ctx *c, const double *grad_caller) {
   CK(cudaMemsetAsync(c->d.t, 0, sizeof(double) * c->d.ninst, c->stream));
   CK(cudaMemsetAsync(c->d.dt, 0, sizeof(double) * c->d.ninst, c->stream));
   CK(cudaMemsetAsync(c->d.status, 0, sizeof(int), c->stream));
+  CK(cudaMemsetAsync(c->d.gate_count, 0, 2 * sizeof(unsigned long long), c->stream));
+  // no gate decisions yet: the first reconstruction is the plain one
+  CK(cudaMemsetAsync(c->d.gate_mask, 0, (c->cs / TW) * sizeof(unsigned), c->stream));
   k_cfl<<<blocks(c->d.nt, 128), 128, 0, c->stream>>>(c->d, p);
   CK(cudaGetLastError());
   c->phase = 0;
@@ -787,6 +880,11 @@ int gks2l_bind(gks2l_ctx *c, void *d_workspace, size_t bytes, void *stream) {
       (rc = upload_form(c, c->d.exiR, P.exiR, 1, false)) || (rc = upload_form(c, c->d.en, en, 1, false)))
     return rc;
   if ((rc = make_maps(c))) return rc;
+  {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev));
+  }
   CK(cudaFuncSetAttribute(k_recon<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileLayout<float>::BYTES));
   CK(cudaFuncSetAttribute(k_recon<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileLayout<double>::BYTES));
   c->bound = true;
@@ -1007,13 +1105,55 @@ int gks2l_alu_peaks(gks2l_ctx *c, double tflops[2]) {
 }
 
 int gks2l_set_mlp(gks2l_ctx *c, const float *params, size_t n_floats) {
-  (void)c; (void)params; (void)n_floats;
-  return GKS2L_ENOTIMPL;
+  if (!c || !params || n_floats != (size_t)MLP_NPARAM) return GKS2L_EINVAL;
+  if (!c->bound) return GKS2L_ESTATE;
+  if (!(c->par.indicator_threshold > 0.f && c->par.indicator_threshold < 1.f)) return GKS2L_EINVAL;
+  for (size_t i = 0; i < n_floats; i++)
+    if (!std::isfinite(params[i])) return GKS2L_EINVAL;
+  float *tmp = nullptr;
+  CK(cudaMallocAsync((void **)&tmp, n_floats * sizeof(float), c->stream));
+  CK(cudaMemcpyAsync(tmp, params, n_floats * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  const double t = c->par.indicator_threshold;
+  k_mlp_pack<<<1, 256, 0, c->stream>>>(tmp, (float)std::log(t / (1.0 - t)), (MlpDev *)c->d.mlp);
+  CK(cudaGetLastError());
+  CK(cudaFreeAsync(tmp, c->stream));
+  CK(cudaMemsetAsync(c->d.gate_mask, 0, (c->cs / TW) * sizeof(unsigned), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->has_mlp = true;
+  drop_graph(c);   // the captured step carries the gate switch
+  return GKS2L_OK;
 }
 
-int gks2l_harvest(gks2l_ctx *c, float tol, float *d_features, float *d_labels) {
-  (void)c; (void)tol; (void)d_features; (void)d_labels;
-  return GKS2L_ENOTIMPL;
+int gks2l_harvest(gks2l_ctx *c, float tol, float *d_features, float *d_labels, float *d_logits) {
+  if (!c || !d_features || !d_labels || !(tol >= 0.f)) return GKS2L_EINVAL;
+  if (!c->bound || !c->has_state) return GKS2L_ESTATE;
+  if (d_logits && !c->has_mlp) return GKS2L_ESTATE;
+  Par p = make_par(c);
+  p.harvest = 1;
+  float *ldev = nullptr;
+  const size_t nt = c->prep.nt;
+  if (d_logits) {
+    CK(cudaMallocAsync((void **)&ldev, nt * sizeof(float), c->stream));
+    p.logit_out = ldev;
+  }
+  // reconstruct the current state of every instance; the labels come from
+  // the plain nonlinear weights, and the gate (if its logits are asked for)
+  // runs on the same right-hand sides
+  p.all_active = 1;
+  p.use_gate = d_logits ? 1 : 0;
+  if (c->par.precision == GKS2L_FP32) {
+    launch_recon<float>(c, p);
+    k_harvest<float><<<blocks(nt, 128), 128, 0, c->stream>>>(c->d, c->d_perm, tol, ldev, d_features, d_labels,
+                                                             d_logits);
+  } else {
+    launch_recon<double>(c, p);
+    k_harvest<double><<<blocks(nt, 128), 128, 0, c->stream>>>(c->d, c->d_perm, tol, ldev, d_features, d_labels,
+                                                              d_logits);
+  }
+  CK(cudaGetLastError());
+  if (ldev) CK(cudaFreeAsync(ldev, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return GKS2L_OK;
 }
 
 const char *gks2l_error_string(int code) {

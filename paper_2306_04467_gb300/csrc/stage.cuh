@@ -63,7 +63,10 @@ struct Dev {
   double *Wn, *Ln, *Ltn;    // stage snapshot (FP64)
   void *coef;               // reconstruction deviations [v*10+k][cell], type R
   void *omg;                // omega_H / gamma_H of eta1 [0] and h2 [1], type R
-  uint8_t *gate;            // 1 = smooth by the learned indicator
+  const void *mlp;          // gate network, packed image (MlpDev)
+  unsigned *gate_mask;      // per tile of 32 cells: bit i = cell i takes the linear weights
+                            // (written by one reconstruction for the next)
+  float *wdev;              // [6][cell] max_k |omega_k / gamma_k - 1| (harvesting)
   // per edge
   const int *eL, *eR;
   const int8_t *exf;
@@ -88,7 +91,10 @@ struct Dev {
 struct Par {
   double g, chi, cfl, eps, eps_num, gam_hi, weno_eps;
   float gf, chif, epsf, eps_numf, gam_hif;   // the same in single precision
-  int use_gate;
+  int use_gate;                              // learned gate active
+  float *logit_out;                          // gate logits per cell (device order), or null
+  int all_active;                            // reconstruct every instance (harvesting)
+  int harvest;                               // record the weights' departure from linear
 };
 
 // a parameter in the form's precision
@@ -174,9 +180,6 @@ __host__ __device__ __forceinline__ void img_dg(const Dev &d, int v, int c, int 
 }
 
 // --------------------------------------------------- compact reconstruction
-// One cell and one variable: P3 least squares (Eq. Recons-system), three P1
-// candidates on {cell, face neighbour}, smoothness indicators and WENO-Z
-// weights, combined polynomial written as deviations in the Taylor basis.
 // Per-cell operator rows of one cell: element k of row r is at
 // base[r * stride + idx] (global arrays: stride = cell stride, idx = cell;
 // a staged shared-memory tile: stride = tile width, idx = cell in the tile).
@@ -198,13 +201,16 @@ __host__ __device__ __forceinline__ CellOps<R> global_ops(const Dev &d, int j) {
 // One cell and one variable: P3 least squares (Eq. Recons-system), three P1
 // candidates on {cell, face neighbour}, smoothness indicators and WENO-Z
 // weights, combined polynomial written as deviations in the Taylor basis.
+// Three steps: gather the right-hand side, solve the P3 fit, then combine
+// (where the troubled-cell gate can choose the linear weights).
+
+// right-hand side: stencil average differences, then h-scaled gradients of
+// the cell and its three face neighbours
 template <typename R>
-__host__ __device__ inline void recon_unit(const Dev &d, const Par &p, const CellOps<R> &o, int j, int v) {
+__host__ __device__ inline void recon_gather(const Dev &d, const CellOps<R> &o, int j, int v, R rhs[NCOL]) {
   const int N = d.cs, S = o.stride, I = o.idx;
-  R *coef = (R *)d.coef;
   const R q0 = ((const R *)d.dq)[v * N + j];
   const R hs = ((const R *)d.hsR)[j];
-  R rhs[NCOL];
   for (int s = 0; s < NSLOT; s++) {
     int c = o.st[s * S + I];
     rhs[s] = c >= 0 ? img_dq<R>(d, v, c, o.sx[s * S + I]) - q0 : (R)0;
@@ -218,15 +224,27 @@ __host__ __device__ inline void recon_unit(const Dev &d, const Par &p, const Cel
     rhs[11 + 2 * f] = hs * g[0];
     rhs[12 + 2 * f] = hs * g[1];
   }
-  R a[9];
+}
+
+// P3 least-squares coefficients a = M rhs
+template <typename R>
+__host__ __device__ inline void recon_p3(const CellOps<R> &o, const R rhs[NCOL], R a[9]) {
+  const int S = o.stride, I = o.idx;
   for (int r = 0; r < 9; r++) {
     R s = 0;
     for (int c = 0; c < NCOL; c++) s += o.lsq[(r * NCOL + c) * S + I] * rhs[c];
     a[r] = s;
   }
+}
+
+template <typename R>
+__host__ __device__ inline void recon_finish(const Dev &d, const Par &p, const CellOps<R> &o, int j, int v,
+                                             const R rhs[NCOL], const R a[9], bool linear) {
+  const int N = d.cs, S = o.stride, I = o.idx;
+  R *coef = (R *)d.coef;
+  const R q0 = ((const R *)d.dq)[v * N + j];
   const R gh = pv<R>(p.gam_hi, p.gam_hif), gl = ((R)1 - gh) * (R)(1.0 / 3.0);
   R fac = 1, wf[3] = {gl, gl, gl}, b[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-  const bool linear = p.use_gate && d.gate[j];
   if (!linear) {
     R beta[4];
     for (int f = 0; f < 3; f++) {
@@ -260,6 +278,16 @@ __host__ __device__ inline void recon_unit(const Dev &d, const Par &p, const Cel
     R iw = 1 / ws;
     fac = w[0] * iw / gh;
     for (int f = 0; f < 3; f++) wf[f] = w[1 + f] * iw;
+    if (p.harvest) {
+      R dv = r_abs<R>(fac - 1);
+      for (int f = 0; f < 3; f++) {
+        R df = r_abs<R>(wf[f] / gl - 1);
+        dv = df > dv ? df : dv;
+      }
+      d.wdev[v * N + j] = (float)dv;
+    }
+  } else if (p.harvest) {
+    d.wdev[v * N + j] = 0.f;
   }
   // R = (w_H / g_H)(P3 - sum g_m P1_m) + sum w_m P1_m
   R r[10];
@@ -275,6 +303,15 @@ __host__ __device__ inline void recon_unit(const Dev &d, const Par &p, const Cel
   for (int k = 0; k < 10; k++) coef[(v * NCOEF + k) * N + j] = r[k];
   if (v == 3) ((R *)d.omg)[j] = fac;
   if (v == 0) ((R *)d.omg)[N + j] = fac;
+}
+
+template <typename R>
+__host__ __device__ inline void recon_unit(const Dev &d, const Par &p, const CellOps<R> &o, int j, int v,
+                                           bool linear) {
+  R rhs[NCOL], a[9];
+  recon_gather<R>(d, o, j, v, rhs);
+  recon_p3<R>(o, rhs, a);
+  recon_finish<R>(d, p, o, j, v, rhs, a, linear);
 }
 
 // ------------------------------------------------- evaluation at an edge point

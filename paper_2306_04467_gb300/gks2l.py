@@ -22,6 +22,8 @@ GKS2L_INDICATOR_MLP = 1
 GKS2L_BC_INTERIOR = 0
 GKS2L_BC_WALL = 1
 GKS2L_BC_PERIODIC = 2
+GKS2L_MLP_NPARAM = 1937
+GKS2L_MLP_NTRAIN = 1889
 
 # every entry point the header declares, with (restype, argtypes)
 _P = ctypes.c_void_p
@@ -62,7 +64,10 @@ SIGNATURES = {
     "gks2l_profile_kernels": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double * 5)]),
     "gks2l_alu_peaks": (_I, [_P, ctypes.POINTER(ctypes.c_double * 2)]),
     "gks2l_set_mlp": (_I, [_P, _P, ctypes.c_size_t]),
-    "gks2l_harvest": (_I, [_P, ctypes.c_float, _P, _P]),
+    "gks2l_harvest": (_I, [_P, ctypes.c_float, _P, _P, _P]),
+    "gks2l_mlp_grad": (_I, [_P, _P, ctypes.c_int32, _P, ctypes.c_float, _P, _P, _P]),
+    "gks2l_mlp_adam": (_I, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_float, _P]),
+    "gks2l_mlp_forward": (_I, [_P, ctypes.c_int32, _P, _P, _P]),
     "gks2l_cfl_mass_noalloc": (_I, [ctypes.c_int32, _P, _P, _P, _D, _D, _P, _P]),
     "gks2l_error_string": (ctypes.c_char_p, [_I]),
     "gks2l_destroy": (None, [_P]),
@@ -224,9 +229,18 @@ class Solver:
         p = np.ascontiguousarray(params_f32, dtype=np.float32)
         _check(load().gks2l_set_mlp(self._h, _np_ptr(p), p.size), "gks2l_set_mlp")
 
-    def harvest(self, tol, features, labels):
-        _check(load().gks2l_harvest(self._h, float(tol), _P(features.data_ptr()), _P(labels.data_ptr())),
-               "gks2l_harvest")
+    def harvest(self, tol, features=None, labels=None, logits=None):
+        """Gate training data of the current state (device tensors, caller's
+        cell order): features [n_tri, 24], labels [n_tri], optionally the fused
+        gate's logits [n_tri]. Allocates what is not given; returns the three."""
+        n, torch = self.n_tri, self.torch
+        if features is None:
+            features = torch.empty((n, 24), dtype=torch.float32, device=self.device)
+        if labels is None:
+            labels = torch.empty(n, dtype=torch.float32, device=self.device)
+        _check(load().gks2l_harvest(self._h, float(tol), _P(features.data_ptr()), _P(labels.data_ptr()),
+                                    _P(logits.data_ptr()) if logits is not None else None), "gks2l_harvest")
+        return features, labels, logits
 
     def close(self):
         if getattr(self, "_h", None):
@@ -247,6 +261,27 @@ def cfl_mass_noalloc(avg, area, dX, g, cfl, out, stream=None):
     s = _P(stream.cuda_stream) if stream is not None else None
     _check(load().gks2l_cfl_mass_noalloc(n, _P(avg.data_ptr()), _P(area.data_ptr()), _P(dX.data_ptr()),
                                          float(g), float(cfl), _P(out.data_ptr()), s), "gks2l_cfl_mass_noalloc")
+
+
+def _sp(stream):
+    return _P(stream.cuda_stream) if stream is not None else None
+
+
+def mlp_grad(X, y, params, pos_weight, grads, loss, stream=None):
+    """Summed loss gradient of the gate network on device tensors."""
+    _check(load().gks2l_mlp_grad(_P(X.data_ptr()), _P(y.data_ptr()), int(y.numel()), _P(params.data_ptr()),
+                                 float(pos_weight), _P(grads.data_ptr()), _P(loss.data_ptr()), _sp(stream)),
+           "gks2l_mlp_grad")
+
+
+def mlp_adam(params, grads, m, v, step, lr, scale, stream=None):
+    _check(load().gks2l_mlp_adam(_P(params.data_ptr()), _P(grads.data_ptr()), _P(m.data_ptr()), _P(v.data_ptr()),
+                                 int(step), float(lr), float(scale), _sp(stream)), "gks2l_mlp_adam")
+
+
+def mlp_forward(X, params, logits, stream=None):
+    _check(load().gks2l_mlp_forward(_P(X.data_ptr()), int(logits.numel()), _P(params.data_ptr()),
+                                    _P(logits.data_ptr()), _sp(stream)), "gks2l_mlp_forward")
 
 
 def problem_solver(prob, precision=GKS2L_FP64, **kw):

@@ -410,3 +410,34 @@ def internal_wave_ridge(nx: int = 5656, ny: int = 707, seed: int = 2311, quad: i
     grad[0, 0] = -egx
     del zero
     return Problem("internal_wave_ridge", mesh, bv, avg, grad, g=9.81, chi=0.97, cfl=0.5)
+
+
+# ---------------------------------------------------------------------------
+# troubled-cell gate: seeded network parameters and synthetic samples
+# ---------------------------------------------------------------------------
+GATE_IN, GATE_H = 24, 32
+GATE_NPARAM = GATE_H * GATE_IN + GATE_H + GATE_H * GATE_H + GATE_H + GATE_H + 1 + 2 * GATE_IN
+
+
+def gate_init(seed: int = 2312) -> np.ndarray:
+    """Float32 parameter vector W1[32][24], b1, W2[32][32], b2, w3, b3, mean[24],
+    inv_std[24]: He-scaled normal weights, zero biases, mean 0, inv_std 1."""
+    z = normal01(seed, GATE_H * GATE_IN + GATE_H * GATE_H + GATE_H)
+    P = np.zeros(GATE_NPARAM, dtype=np.float64)
+    o = 0
+    P[o:o + GATE_H * GATE_IN] = z[:GATE_H * GATE_IN] * math.sqrt(2.0 / GATE_IN)
+    o += GATE_H * GATE_IN + GATE_H
+    P[o:o + GATE_H * GATE_H] = z[GATE_H * GATE_IN:GATE_H * (GATE_IN + GATE_H)] * math.sqrt(2.0 / GATE_H)
+    o += GATE_H * GATE_H + GATE_H
+    P[o:o + GATE_H] = z[GATE_H * (GATE_IN + GATE_H):] * math.sqrt(1.0 / GATE_H)
+    o += GATE_H + 1
+    P[o + GATE_IN:] = 1.0
+    return P.astype(np.float32)
+
+
+def gate_samples(n: int, seed: int = 2313, scale: float = 0.4):
+    """n synthetic gate inputs (float32 [n][24], normal with the given scale,
+    clipped to [-1, 1] like the normalised features) and Bernoulli(0.3) labels."""
+    X = np.clip(scale * normal01(seed, n * GATE_IN).reshape(n, GATE_IN), -1.0, 1.0).astype(np.float32)
+    y = (uniform01(seed + 1, n) < 0.3).astype(np.float32)
+    return X, y
