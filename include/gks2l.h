@@ -162,9 +162,11 @@ int gks2l_stats(gks2l_ctx *ctx, gks2l_stats_t *out);
  * A 24 -> 32 -> 32 -> 1 MLP (ReLU hidden layers, sigmoid output) predicts per
  * cell whether the nonlinear WENO weights of the reconstruction would depart
  * from the linear ones; cells it calls smooth take the linear P3
- * reconstruction and a blending weight w = 1. The network runs inside each
- * reconstruction and its decisions apply to the next one (the first stage
- * after gks2l_set_state or gks2l_set_mlp is the plain method). Parameters are a float vector
+ * reconstruction and a blending weight w = 1. The network runs on a second
+ * stream beside each stage's interface and edge kernels, on the state that
+ * stage reconstructed, and its decisions apply to the next reconstruction
+ * (the first stage after gks2l_set_state or gks2l_set_mlp is the plain
+ * method). gks2l_set_mlp creates that stream. Parameters are a float vector
  * of GKS2L_MLP_NPARAM entries:
  *   W1[32][24], b1[32], W2[32][32], b2[32], w3[32], b3, mean[24], inv_std[24]
  * (the first GKS2L_MLP_NTRAIN are trained; features are (x - mean) * inv_std).
@@ -195,7 +197,9 @@ int gks2l_harvest(gks2l_ctx *ctx, float tol, float *d_features, float *d_labels,
  *   L = sum_i pos_weight y_i softplus(-s_i) + (1 - y_i) softplus(s_i)
  * of n samples (device d_X[n][24], d_y[n] in {0, 1}) for parameters d_params
  * (device, GKS2L_MLP_NPARAM floats): writes d_grads[GKS2L_MLP_NTRAIN] (sums
- * over the samples) and d_loss[1]. BF16 tensor cores, FP32 sums. */
+ * over the samples) and d_loss[1]. BF16 tensor cores, FP32 sums in a fixed
+ * order (the result is reproducible). Takes stream-ordered scratch of about
+ * 7.6 KB per 64 samples (at most 18 MB). */
 int gks2l_mlp_grad(const float *d_X, const float *d_y, int32_t n, const float *d_params, float pos_weight,
                    float *d_grads, float *d_loss, void *stream);
 
@@ -214,8 +218,10 @@ int gks2l_mlp_forward(const float *d_X, int32_t n, const float *d_params, float 
  * one between CUDA events on the bound stream, then synchronises. ms[k] is
  * the mean duration of one launch of kernel k, in the order: reconstruction,
  * interface levels, edge solution, cell update (each averaged over both
- * stages), step start. Requires a state and phase at a step boundary. */
-int gks2l_profile_kernels(gks2l_ctx *ctx, int32_t n_steps, double ms[5]);
+ * stages), step start, troubled-cell gate (0 when it is off; run here in
+ * sequence, in gks2l_advance beside the interface and edge kernels).
+ * Requires a state and phase at a step boundary. */
+int gks2l_profile_kernels(gks2l_ctx *ctx, int32_t n_steps, double ms[6]);
 
 /* Measurement helper with no counterpart in the paper: FP32 and FP64 FMA
  * throughput of the bound device (TFLOP/s, FMA = 2 flops) from FMA-chain

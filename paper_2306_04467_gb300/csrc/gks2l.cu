@@ -51,8 +51,7 @@ template <typename R> struct TileLayout {
   static constexpr unsigned ST = MM + 7 * TW * sizeof(R);
   static constexpr unsigned SX = ST + kSlots * TW * 4;
   static constexpr unsigned BAR = SX + 384;                   // 9 * 32 int8 rounded to 128 B
-  static constexpr unsigned XT = BAR + 128;                   // gate features, [32][GATE_LD] bf16
-  static constexpr unsigned BYTES = XT + 32 * GATE_LD * 2;
+  static constexpr unsigned BYTES = BAR + 16;
   static constexpr unsigned TX = BAR - 96;                    // bytes the six copies deliver
   static constexpr unsigned TX_LINEAR = TX - (MM - P1);       // without the P1 and beta rows
 };
@@ -153,41 +152,48 @@ __global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p,
       atomicAdd(&d.gate_count[1], (unsigned long long)nc);
     }
   }
-  R rhs[NCOL], a[9];
-  if (active) {
-    recon_gather<R>(d, o, j, v, rhs);
-    recon_p3<R>(o, rhs, a);
-    recon_finish<R>(d, p, o, j, v, rhs, a, linear);
-  }
-  if (!p.use_gate || (v != 0 && v != 3)) return;
-  // The gate for the next reconstruction of these cells: the h2 and eta1
-  // warps turn their right-hand sides into the 24 features, meet at a named
-  // barrier, and each runs the network on the tensor cores for 16 cells
-  // (weights read through L1); each writes its half of the tile's mask.
+  if (active) recon_unit<R>(d, p, o, j, v, linear);
+}
+
+// Troubled-cell gate (not part of the paper). It runs on a second stream
+// beside the interface and edge kernels of a stage, on the state that stage
+// reconstructed, and leaves for the next reconstruction the mask of cells it
+// calls smooth. Persistent warps keep the network in registers and walk over
+// tiles of 32 cells: the 24 features of each cell go to a shared-memory tile,
+// the network runs on the tensor cores, and the warp writes the tile's mask
+// (cells past the end or of finished instances count as smooth).
+constexpr int GATE_BLOCKS_PER_SM = 2;
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_gate(Dev d, Par p) {
+  __shared__ __align__(16) __nv_bfloat16 Xs[4][32 * GATE_LD];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const MlpDev &w = *reinterpret_cast<const MlpDev *>(d.mlp);
-  __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(sm + T::XT);
-  unsigned *row = reinterpret_cast<unsigned *>(X + threadIdx.x * GATE_LD);
-  {
-    float f[12];
+  MlpFrags F;
+  mlp_frags(F, w, lane);
+  __nv_bfloat16 *X = Xs[wid];
+  unsigned *row = reinterpret_cast<unsigned *>(X + lane * GATE_LD);
+  for (int k = 12; k < 16; k++) row[k] = 0u;   // columns 24..31 stay zero
+  const int ntile = (d.nt + TW - 1) / TW;
+  for (int tile = blockIdx.x * 4 + wid; tile < ntile; tile += gridDim.x * 4) {
+    const int j = tile * TW + lane;
+    const bool active = j < d.nt && (p.all_active || d.dt[d.inst[j]] > 0);
+    float f[24];
     if (active) {
-      gate_features_rhs<R>(d, j, v, rhs, f);
+      gate_features<R>(d, j, d.st_cell, d.st_xf, d.cs, j, f);
     } else {
-      for (int k = 0; k < 12; k++) f[k] = 0.f;
+      for (int k = 0; k < 24; k++) f[k] = 0.f;
     }
-    // the image has the normalisation folded into the first layer
-    const int off = v == 3 ? 0 : 6;
-    for (int k = 0; k < 6; k++) row[off + k] = pack_bf16(f[2 * k], f[2 * k + 1]);
-    if (v == 0)
-      for (int k = 12; k < 16; k++) row[k] = 0u;   // columns 24..31
+    // the image has the input normalisation folded into the first layer
+    for (int k = 0; k < 12; k++) row[k] = pack_bf16(f[2 * k], f[2 * k + 1]);
+    __syncwarp();
+    const float logit = mlp_tile32(F, X, GATE_LD, lane);
+    const bool smooth = active && logit < F.threshold;
+    const unsigned mask = __ballot_sync(FULL, smooth || !active);
+    if (lane == 0) d.gate_mask[tile] = mask;
+    if (p.logit_out && j < d.nt) p.logit_out[j] = logit;
+    __syncwarp();   // the tile is rewritten next
   }
-  asm volatile("bar.sync 1, 64;" ::: "memory");
-  const int lane = threadIdx.x, mt = v == 0 ? 0 : 1, r = 16 * mt + (lane & 15), jr = j0 + r;
-  const float logit = mlp_rows16(w, X, GATE_LD, mt, lane);
-  const bool row_active = jr < d.nt && (p.all_active || d.dt[d.inst[jr]] > 0);
-  const bool smooth = lane < 16 && row_active && logit < w.threshold;
-  const unsigned bits = __ballot_sync(FULL, smooth || (lane < 16 && !row_active)) & 0xffffu;
-  if (lane == 0) reinterpret_cast<unsigned short *>(d.gate_mask)[2 * blockIdx.x + mt] = (unsigned short)bits;
-  if (lane < 16 && p.logit_out && jr < d.nt) p.logit_out[jr] = logit;
 }
 
 // gate network image for the reconstruction blocks (one block)
@@ -474,6 +480,8 @@ struct gks2l_ctx {
   std::vector<double> bmean_h; // cell-average bottom (device order), host copy
   bool has_mlp = false;
   int n_sm = 1;                // SMs of the bound device
+  cudaStream_t side = nullptr; // second stream for the gate (created with the network)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int phase = 0;
   int64_t stages = 0;
   cudaGraph_t graph = nullptr;
@@ -659,6 +667,12 @@ int make_maps(gks2l_ctx *c) {
 }
 
 template <typename R>
+void launch_gate(gks2l_ctx *c, const Par &p, cudaStream_t st) {
+  const unsigned nb = std::min(blocks(c->d.nt, 4 * TW), (unsigned)(c->n_sm * GATE_BLOCKS_PER_SM));
+  k_gate<R><<<nb, 128, 0, st>>>(c->d, p);
+}
+
+template <typename R>
 void launch_recon(gks2l_ctx *c, const Par &p) {
   const Dev &d = c->d;
   k_recon<R><<<blocks(d.nt, TW), dim3(TW, 6), TileLayout<R>::BYTES, c->stream>>>(d, p, c->maps);
@@ -669,8 +683,17 @@ void launch_stage(gks2l_ctx *c, int stage) {
   const Dev &d = c->d;
   Par p = make_par(c);
   launch_recon<R>(c, p);
+  if (p.use_gate) {
+    // the gate for the next stage reads this stage's state, which k_update
+    // replaces: it runs beside k_iface and k_edge and joins before k_update
+    cudaEventRecord(c->ev_fork, c->stream);
+    cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    launch_gate<R>(c, p, c->side);
+    cudaEventRecord(c->ev_join, c->side);
+  }
   k_iface<R><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d);
   k_edge<R><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d, p, stage);
+  if (p.use_gate) cudaStreamWaitEvent(c->stream, c->ev_join, 0);
   k_update<R><<<blocks(d.nt, 128), 128, 0, c->stream>>>(d, p, stage);
 }
 
@@ -1022,14 +1045,14 @@ int gks2l_stats(gks2l_ctx *c, gks2l_stats_t *out) {
   return GKS2L_OK;
 }
 
-int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[5]) {
+int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[6]) {
   if (!c || !ms || n_steps <= 0) return GKS2L_EINVAL;
   if (!c->bound || !c->has_state || c->phase != 0) return GKS2L_ESTATE;
   double zero = 0.0;
   CK(cudaMemcpyAsync(c->d_tend, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  cudaEvent_t ev[7];
-  for (int i = 0; i < 7; i++) CK(cudaEventCreate(&ev[i]));
-  double acc[5] = {0, 0, 0, 0, 0};
+  cudaEvent_t ev[8];
+  for (int i = 0; i < 8; i++) CK(cudaEventCreate(&ev[i]));
+  double acc[6] = {0, 0, 0, 0, 0, 0};
   const Dev &d = c->d;
   Par p = make_par(c);
   const bool f32 = c->par.precision == GKS2L_FP32;
@@ -1042,6 +1065,11 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[5]) {
       if (f32) launch_recon<float>(c, p);
       else launch_recon<double>(c, p);
       CK(cudaEventRecord(ev[3], c->stream));
+      if (p.use_gate) {
+        if (f32) launch_gate<float>(c, p, c->stream);
+        else launch_gate<double>(c, p, c->stream);
+      }
+      CK(cudaEventRecord(ev[7], c->stream));
       if (f32) k_iface<float><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d);
       else k_iface<double><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d);
       CK(cudaEventRecord(ev[4], c->stream));
@@ -1053,7 +1081,13 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[5]) {
       CK(cudaEventRecord(ev[6], c->stream));
       CK(cudaEventSynchronize(ev[6]));
       float t;
-      for (int k = 0; k < 4; k++) {
+      CK(cudaEventElapsedTime(&t, ev[2], ev[3]));
+      acc[0] += t;
+      CK(cudaEventElapsedTime(&t, ev[3], ev[7]));
+      acc[5] += t;
+      CK(cudaEventElapsedTime(&t, ev[7], ev[4]));
+      acc[1] += t;
+      for (int k = 2; k < 4; k++) {
         CK(cudaEventElapsedTime(&t, ev[2 + k], ev[3 + k]));
         acc[k] += t;
       }
@@ -1063,9 +1097,10 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[5]) {
     acc[4] += t0;
   }
   CK(cudaGetLastError());
-  for (int i = 0; i < 7; i++) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 8; i++) cudaEventDestroy(ev[i]);
   for (int k = 0; k < 4; k++) ms[k] = acc[k] / (2.0 * n_steps);
   ms[4] = acc[4] / n_steps;
+  ms[5] = acc[5] / (2.0 * n_steps);
   c->stages += 2 * n_steps;
   return GKS2L_OK;
 }
@@ -1110,6 +1145,11 @@ int gks2l_set_mlp(gks2l_ctx *c, const float *params, size_t n_floats) {
   if (!(c->par.indicator_threshold > 0.f && c->par.indicator_threshold < 1.f)) return GKS2L_EINVAL;
   for (size_t i = 0; i < n_floats; i++)
     if (!std::isfinite(params[i])) return GKS2L_EINVAL;
+  if (!c->side) {
+    CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  }
   float *tmp = nullptr;
   CK(cudaMallocAsync((void **)&tmp, n_floats * sizeof(float), c->stream));
   CK(cudaMemcpyAsync(tmp, params, n_floats * sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -1140,8 +1180,14 @@ int gks2l_harvest(gks2l_ctx *c, float tol, float *d_features, float *d_labels, f
   // the plain nonlinear weights, and the gate (if its logits are asked for)
   // runs on the same right-hand sides
   p.all_active = 1;
-  p.use_gate = d_logits ? 1 : 0;
-  if (c->par.precision == GKS2L_FP32) {
+  p.use_gate = 0;
+  const bool f32 = c->par.precision == GKS2L_FP32;
+  if (d_logits) {
+    if (f32) launch_gate<float>(c, p, c->stream);
+    else launch_gate<double>(c, p, c->stream);
+  }
+  p.logit_out = nullptr;
+  if (f32) {
     launch_recon<float>(c, p);
     k_harvest<float><<<blocks(nt, 128), 128, 0, c->stream>>>(c->d, c->d_perm, tol, ldev, d_features, d_labels,
                                                              d_logits);
@@ -1176,6 +1222,9 @@ const char *gks2l_error_string(int code) {
 void gks2l_destroy(gks2l_ctx *c) {
   if (!c) return;
   drop_graph(c);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
 }
 

@@ -7,7 +7,9 @@
 // over a batch; each warp takes 16 samples at a time. Layer outputs stay in
 // registers and are reused as the A operand of the next product; the weight
 // gradients dW = dZ^T H are products over the batch dimension, read
-// transposed from a per-warp shared-memory tile. Sums are FP32.
+// transposed from a per-warp shared-memory tile. Sums are FP32, in a fixed
+// order (per-warp partials, then a reduction in warp order): the gradient is
+// the same from run to run.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -49,8 +51,13 @@ __device__ __forceinline__ void load_b_t(unsigned b[2], const __nv_bfloat16 *T, 
   b[1] = pack2(T[(c + 8) * 32 + n0 + g], T[(c + 9) * 32 + n0 + g]);
 }
 
+// Each warp writes its partial sums (NTRAIN gradients, then the loss) to
+// part[warp]; k_mlp_reduce adds them up in warp order, so the result does not
+// depend on scheduling.
+constexpr int NPART = MLP_NTRAIN + 1;
+
 __global__ void __launch_bounds__(TPB) k_mlp_grad(const float *X, const float *y, int n, const float *P, float pos_w,
-                                                  float *grads, float *loss_out) {
+                                                  float *part) {
   __shared__ MlpDev w;
   __shared__ WarpTiles tiles[TPB / 32];
   mlp_pack(w, P, 0.f, threadIdx.x, TPB);
@@ -213,26 +220,36 @@ __global__ void __launch_bounds__(TPB) k_mlp_grad(const float *X, const float *y
     gb3 += __shfl_xor_sync(0xffffffffu, gb3, o);
     lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
   }
+  float *out = part + (size_t)(blockIdx.x * (TPB / 32) + wid) * NPART;
   if (lane < 4) {
     for (int nt = 0; nt < 4; nt++)
       for (int i = 0; i < 2; i++) {
         int col = 8 * nt + c + i;
-        atomicAdd(&grads[MLP_B1 + col], gb1[nt][i]);
-        atomicAdd(&grads[MLP_B2 + col], gb2[nt][i]);
-        atomicAdd(&grads[MLP_W3 + col], gw3[nt][i]);
+        out[MLP_B1 + col] = gb1[nt][i];
+        out[MLP_B2 + col] = gb2[nt][i];
+        out[MLP_W3 + col] = gw3[nt][i];
       }
   }
   if (lane == 0) {
-    atomicAdd(&grads[MLP_B3], gb3);
-    atomicAdd(loss_out, lsum);
+    out[MLP_B3] = gb3;
+    out[MLP_NTRAIN] = lsum;
   }
   for (int mt = 0; mt < 2; mt++)
     for (int nt = 0; nt < 4; nt++)
       for (int i = 0; i < 4; i++) {
-        int out = 16 * mt + g + (i >= 2 ? 8 : 0), in = 8 * nt + c + (i & 1);
-        atomicAdd(&grads[MLP_W2 + out * MLP_H + in], gW2[mt][nt][i]);
-        if (in < MLP_IN) atomicAdd(&grads[MLP_W1 + out * MLP_IN + in], gW1[mt][nt][i]);
+        int o = 16 * mt + g + (i >= 2 ? 8 : 0), in = 8 * nt + c + (i & 1);
+        out[MLP_W2 + o * MLP_H + in] = gW2[mt][nt][i];
+        if (in < MLP_IN) out[MLP_W1 + o * MLP_IN + in] = gW1[mt][nt][i];
       }
+}
+
+__global__ void k_mlp_reduce(const float *part, int nparts, float *grads, float *loss_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NPART) return;
+  float s = 0.f;
+  for (int w = 0; w < nparts; w++) s += part[(size_t)w * NPART + i];
+  if (i < MLP_NTRAIN) grads[i] = s;
+  else *loss_out = s;
 }
 
 __global__ void k_mlp_adam(float *P, const float *G, float *M, float *V, int n, int step, float lr, float scale) {
@@ -286,12 +303,16 @@ extern "C" int gks2l_mlp_grad(const float *d_X, const float *d_y, int32_t n, con
                               float *d_grads, float *d_loss, void *stream) {
   if (n <= 0 || !d_X || !d_y || !d_params || !d_grads || !d_loss) return GKS2L_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(d_grads, 0, MLP_NTRAIN * sizeof(float), s) != cudaSuccess) return GKS2L_ECUDA;
-  if (cudaMemsetAsync(d_loss, 0, sizeof(float), s) != cudaSuccess) return GKS2L_ECUDA;
-  // a few blocks per SM: each warp loops over 16-sample tiles, so the
-  // gradient atomics stay few
-  k_mlp_grad<<<grid_for(n, 16 * (TPB / 32), 608), TPB, 0, s>>>(d_X, d_y, n, d_params, pos_weight, d_grads, d_loss);
-  return cudaGetLastError() == cudaSuccess ? GKS2L_OK : GKS2L_ECUDA;
+  // a few blocks per SM: each warp loops over 16-sample tiles
+  const unsigned grid = grid_for(n, 16 * (TPB / 32), 608);
+  const int nparts = (int)grid * (TPB / 32);
+  float *part = nullptr;
+  if (cudaMallocAsync((void **)&part, (size_t)nparts * NPART * sizeof(float), s) != cudaSuccess) return GKS2L_ECUDA;
+  k_mlp_grad<<<grid, TPB, 0, s>>>(d_X, d_y, n, d_params, pos_weight, part);
+  k_mlp_reduce<<<(NPART + 255) / 256, 256, 0, s>>>(part, nparts, d_grads, d_loss);
+  const bool ok = cudaGetLastError() == cudaSuccess;
+  if (cudaFreeAsync(part, s) != cudaSuccess || !ok) return GKS2L_ECUDA;
+  return GKS2L_OK;
 }
 
 extern "C" int gks2l_mlp_adam(float *d_params, const float *d_grads, float *d_m, float *d_v, int32_t step, float lr,

@@ -67,29 +67,6 @@ __host__ __device__ inline void gate_features(const Dev &d, int j, const int *st
   }
 }
 
-// The 12 features of variable v (3: eta1, 0: h2) from the reconstruction's
-// right-hand side: stencil slots 0-2 are the face neighbours (rhs[f] =
-// q_f - q0), rhs[9..10] and rhs[11 + 2f..12 + 2f] the h-scaled gradients of
-// the cell and of face f. The same numbers as gate_features.
-template <typename R>
-__host__ __device__ inline void gate_features_rhs(const Dev &d, int j, int v, const R *rhs, float out[12]) {
-  const R m = (rhs[0] + rhs[1] + rhs[2]) * (R)0.25;   // four-cell mean minus q0
-  R raw[12], ss = 0;
-  raw[0] = -m;
-  raw[1] = rhs[9];
-  raw[2] = rhs[10];
-  for (int f = 0; f < 3; f++) {
-    raw[3 + 3 * f] = rhs[f] - m;
-    raw[4 + 3 * f] = rhs[11 + 2 * f];
-    raw[5 + 3 * f] = rhs[12 + 2 * f];
-  }
-  for (int k = 0; k < 12; k++) ss += raw[k] * raw[k];
-  R Q0 = ((const R *)d.dq)[v * d.cs + j] + ((const R *)d.refR)[2 * d.inst[j] + (v == 3 ? 1 : 0)];
-  ss += ((const R *)d.epsA)[j] * (1 + Q0 * Q0);
-  R is = (R)1 / r_sqrt<R>(ss);
-  for (int k = 0; k < 12; k++) out[k] = (float)(raw[k] * is);
-}
-
 #ifdef __CUDACC__
 // D = A (16x16 bf16, row) * B (16x8 bf16, col) + D (fp32)
 __device__ __forceinline__ void mma_bf16(float d[4], const unsigned a[4], const unsigned b[2]) {
@@ -210,25 +187,7 @@ __device__ __forceinline__ void frag_w2(const MlpFrags &F, int ks, int nt, int, 
 __device__ __forceinline__ float2 frag_b1(const MlpFrags &F, int nt, int) { return make_float2(F.b1[nt][0], F.b1[nt][1]); }
 __device__ __forceinline__ float2 frag_b2(const MlpFrags &F, int nt, int) { return make_float2(F.b2[nt][0], F.b2[nt][1]); }
 __device__ __forceinline__ float2 frag_w3(const MlpFrags &F, int nt, int) { return make_float2(F.w3[nt][0], F.w3[nt][1]); }
-// the packed network itself (shared or global memory, read at each use)
-__device__ __forceinline__ void frag_w1(const MlpDev &w, int ks, int nt, int lane, unsigned b[2]) {
-  load_b_nk(b, w.w1, 32, 8 * nt, 16 * ks, lane);
-}
-__device__ __forceinline__ void frag_w2(const MlpDev &w, int ks, int nt, int lane, unsigned b[2]) {
-  load_b_nk(b, w.w2, 32, 8 * nt, 16 * ks, lane);
-}
-__device__ __forceinline__ float2 frag_b1(const MlpDev &w, int nt, int lane) {
-  const int col = 8 * nt + (lane & 3) * 2;
-  return make_float2(w.b1[col], w.b1[col + 1]);
-}
-__device__ __forceinline__ float2 frag_b2(const MlpDev &w, int nt, int lane) {
-  const int col = 8 * nt + (lane & 3) * 2;
-  return make_float2(w.b2[col], w.b2[col + 1]);
-}
-__device__ __forceinline__ float2 frag_w3(const MlpDev &w, int nt, int lane) {
-  const int col = 8 * nt + (lane & 3) * 2;
-  return make_float2(w.w3[col], w.w3[col + 1]);
-}
+__device__ __forceinline__ float frag_b3(const MlpFrags &F) { return F.b3; }
 
 template <typename Frags>
 __device__ inline float mlp_rows16(const Frags &F, const __nv_bfloat16 *X, int ld, int mt, int lane) {
@@ -283,7 +242,7 @@ __device__ inline float mlp_rows16(const Frags &F, const __nv_bfloat16 *X, int l
   // rows g (s0) and g + 8 (s1) live on lanes 4g..4g+3
   const int src = (lane & 7) * 4;
   const float v0 = __shfl_sync(0xffffffffu, s0, src), v1 = __shfl_sync(0xffffffffu, s1, src);
-  return (lane < 8 ? v0 : v1) + F.b3;
+  return (lane < 8 ? v0 : v1) + frag_b3(F);
 }
 
 // One warp: logits of 32 cells; lane r returns the logit of row r.

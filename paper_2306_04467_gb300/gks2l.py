@@ -61,7 +61,7 @@ SIGNATURES = {
     "gks2l_get_state": (_I, [_P, _P, _P]),
     "gks2l_get_state_device": (_I, [_P, _P, _P]),
     "gks2l_stats": (_I, [_P, ctypes.POINTER(gks2l_stats_t)]),
-    "gks2l_profile_kernels": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double * 5)]),
+    "gks2l_profile_kernels": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double * 6)]),
     "gks2l_alu_peaks": (_I, [_P, ctypes.POINTER(ctypes.c_double * 2)]),
     "gks2l_set_mlp": (_I, [_P, _P, ctypes.c_size_t]),
     "gks2l_harvest": (_I, [_P, ctypes.c_float, _P, _P, _P]),
@@ -214,10 +214,10 @@ class Solver:
                 "status": s.status, "n_instances": s.n_instances, "smooth_fraction": s.smooth_fraction}
 
     def profile_kernels(self, n_steps):
-        """Mean ms per launch of [recon, iface, edge, update, step_begin]."""
-        ms = (ctypes.c_double * 5)()
+        """Mean ms per launch of recon, iface, edge, update, step_begin, gate."""
+        ms = (ctypes.c_double * 6)()
         _check(load().gks2l_profile_kernels(self._h, int(n_steps), ctypes.byref(ms)), "gks2l_profile_kernels")
-        return {"recon": ms[0], "iface": ms[1], "edge": ms[2], "update": ms[3], "step_begin": ms[4]}
+        return {"recon": ms[0], "iface": ms[1], "edge": ms[2], "update": ms[3], "step_begin": ms[4], "gate": ms[5]}
 
     def alu_peaks(self):
         """Measured FP32 and FP64 FMA throughput of the device, TFLOP/s."""

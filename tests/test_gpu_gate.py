@@ -86,6 +86,18 @@ def test_gradient_matches_oracle(n):
     assert G @ Ge / np.linalg.norm(G) / np.linalg.norm(Ge) >= 0.999
 
 
+def test_gradient_is_reproducible():
+    P = params(8)
+    X, y = inputs.gate_samples(20000, seed=23)
+    out = []
+    for _ in range(2):
+        G = torch.empty(mlp.NTRAIN, dtype=torch.float32, device=DEV)
+        L = torch.empty(1, dtype=torch.float32, device=DEV)
+        g.mlp_grad(dev(X), dev(y), dev(P), 1.5, G, L)
+        out.append((G.cpu().numpy(), L.item()))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
 def test_adam_matches_oracle():
     P = params(9)
     rng = np.random.default_rng(4)
