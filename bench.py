@@ -8,9 +8,11 @@ is one S2O4 time step (two stages) over the whole mesh, i.e. every part of the
 hot path: CFL step, reconstruction, interface levels, edge solution, sources,
 update and gradients.
 
-`value` is the FP32 form (FP64 for the balance terms and sums); the plain FP64
-GPU form of the same workload is reported beside it, with the L1 difference
-between the two after the timed run.
+`value` is the FP32 form (FP64 for the balance terms and sums) with the
+learned troubled-cell gate, trained first on this GPU from the solver's own
+seeded runs; the plain FP32 form and the plain FP64 GPU form of the same
+workload are reported beside it, with the L1 differences to the FP64 form
+after the timed runs and on the smooth periodic case.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -40,21 +42,29 @@ N_SQ = 1024
 
 # Per-unit work of each kernel: (FP32 flops, FP64 flops, algorithmic DRAM
 # bytes). Flops are the hardware counts (sm__sass_thread_inst_executed_op_
-# {f,d}{add,mul,fma}[2] with FMA = 2 flops) of one launch on a 131,072-cell /
-# 197,120-edge case divided by its units; bytes are the minimum one launch must
-# move with the structure-of-arrays layout (each cell or edge record read or
-# written once). Units: cells for recon and update, edges for iface and edge.
+# {f,d}{add,mul,fma}[2] with FMA = 2 flops) of the launches of one step of the
+# benchmark workload at 512 x 512 squares (524,288 cells, 787,456 edges), per
+# unit; the FP32-form reconstruction count is the gated one on this workload
+# (every tile smooth). Bytes are the minimum one launch must move with the
+# structure-of-arrays layout, each cell or edge record read or written once
+# (reconstruction: operators 9x17 + 7 + stencil 9 + gathers + 60 coefficients
+# out, without the P1 and smoothness rows for gated tiles; gate: 3 neighbour
+# ids and transforms, eta1/h2 values and gradients, scales; interface: edge
+# geometry, both cells' coefficients, two levels out; edge: the same plus
+# plane rows and blend weights, 24 interface values out; update: three edges'
+# fluxes and interface values, state in/out with the S2O4 snapshot, mirrors
+# out). Units: cells for recon, gate and update, edges for iface and edge.
 WORK_PER_UNIT = {
-    "fp32": {"recon": (4021, 0, 1417), "iface": (928, 0, 277), "edge": (6981, 0, 514),
-             "update": (0, 343, 850)},
-    "fp64": {"recon": (69, 4593, 2209), "iface": (15, 1349, 473), "edge": (107, 9162, 696),
+    "fp32": {"recon": (2195, 0, 1017), "gate": (280, 0, 51), "iface": (930, 0, 244), "edge": (6981, 0, 366),
+             "update": (331, 73, 570)},
+    "fp64": {"recon": (69, 4593, 2209), "gate": (280, 0, 63), "iface": (15, 1349, 473), "edge": (107, 9162, 696),
              "update": (0, 343, 850)},
 }
 # Measured FMA-chain peaks of this GB300 pool (TFLOP/s, 2 flops per FMA).
 PEAK_TFLOPS = {"fp32": 76.5, "fp64": 1.254}
-# DRAM bytes per unit (dram__bytes_read.sum + dram__bytes_write.sum of one
-# launch on the 131,072-cell case, per unit; traffic grows with the units).
-TRAFFIC_PER_UNIT = {"fp32": {"recon": 1174.0, "iface": 235.0, "edge": 293.0, "update": 431.0}}
+# DRAM bytes per unit (dram__bytes_read.sum + dram__bytes_write.sum of the
+# same launches, per unit; inputs larger than L2, traffic grows with units).
+TRAFFIC_PER_UNIT = {"fp32": {"recon": 971.0, "gate": 51.0, "iface": 245.0, "edge": 357.0, "update": 461.0}}
 
 
 def roofline(form, kernel, units, ms, hbm_gbs):
@@ -199,12 +209,26 @@ def run_profile_case(args):
     from paper_2306_04467_gb300 import gks2l as g
     from paper_2306_04467_gb300 import inputs
     prob = inputs.lake_at_rest(args.profile_case, chi=0.98)
-    prec = g.GKS2L_FP32 if args.form == "fp32" else g.GKS2L_FP64
-    par = g.default_params(g=prob.g, chi=prob.chi, cfl=prob.cfl, precision=prec)
+    prec = g.GKS2L_FP64 if args.form == "fp64" else g.GKS2L_FP32
+    kw = {}
+    if args.form == "fp32_learned":
+        from paper_2306_04467_gb300 import gate
+        P, _ = gate.default_gate()
+        kw = dict(indicator=g.GKS2L_INDICATOR_MLP, indicator_threshold=gate.THRESHOLD)
+    par = g.default_params(g=prob.g, chi=prob.chi, cfl=prob.cfl, precision=prec, **kw)
     s = g.Solver(prob.mesh, par, prob.b_vert)
     s.set_state(prob.avg, prob.grad)
+    if kw:
+        s.set_mlp(P)
+        s.advance(2)   # the first stage after set_mlp is the plain method
+    import torch
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()   # a profiler started with capture off records from here
+    ms = s.profile_kernels(1)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     print(json.dumps({"profile_case": args.profile_case, "form": args.form, "n_tri": prob.mesh.n_tri,
-                      "kernel_ms": s.profile_kernels(1)}))
+                      "kernel_ms": ms}))
 
 
 def main():
@@ -218,7 +242,7 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0,
                     help="profiling mode: one step of the workload at this many squares per side, kernels "
                          "launched one by one (for ncu captures of a small case)")
-    ap.add_argument("--form", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--form", default="fp32", choices=["fp32", "fp32_learned", "fp64"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -256,14 +280,33 @@ def main():
     nt = prob.mesh.n_tri
     n_edges = (3 * nt + 2 * (prob.mesh.nx + prob.mesh.ny)) // 2
     stream = torch.cuda.Stream(device=dev)
+
+    # the learned gate: harvested from the solver's own seeded runs and trained
+    # on this GPU by the library's kernels (outside the timed region)
+    from paper_2306_04467_gb300 import gate
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        gate_params, gate_q = gate.default_gate()
+        torch.cuda.synchronize(dev)
+        gate_train_s = time.perf_counter() - t0
+
+    def solver(p, prec, learned):
+        kw = dict(indicator=g.GKS2L_INDICATOR_MLP, indicator_threshold=gate.THRESHOLD) if learned else {}
+        par = g.default_params(g=p.g, chi=p.chi, cfl=p.cfl, precision=prec, **kw)
+        s = g.Solver(p.mesh, par, p.b_vert, device=dev, stream=stream)
+        s.set_state(p.avg, p.grad)
+        if learned:
+            s.set_mlp(gate_params)
+        return s
+
+    forms = (("fp32_learned", g.GKS2L_FP32, True), ("fp32", g.GKS2L_FP32, False), ("fp64", g.GKS2L_FP64, False))
     results = {}
     live_peaks = None
-    for form, prec in (("fp32", g.GKS2L_FP32), ("fp64", g.GKS2L_FP64)):
+    for form, prec, learned in forms:
         with torch.cuda.stream(stream):
-            par = g.default_params(g=prob.g, chi=prob.chi, cfl=prob.cfl, precision=prec)
-            s = g.Solver(prob.mesh, par, prob.b_vert, device=dev, stream=stream)
-            s.set_state(prob.avg, prob.grad)
-            steps = args.steps if form == "fp32" else max(2, args.steps // 4)
+            s = solver(prob, prec, learned)
+            shapes = s.autotune(1)
+            steps = args.steps if prec == g.GKS2L_FP32 else max(2, args.steps // 4)
             s.advance(2 * args.warmup)
             torch.cuda.synchronize(dev)
             barrier()
@@ -272,10 +315,14 @@ def main():
             sampler = ClockSampler(local)
             with sampler:
                 torch.cuda.synchronize(dev)
+                if form == "fp32_learned":
+                    torch.cuda.profiler.start()   # a profiler started with capture off records the timed region
                 e0.record(stream)
                 s.advance(2 * steps, sync=False)
                 e1.record(stream)
                 torch.cuda.synchronize(dev)
+                if form == "fp32_learned":
+                    torch.cuda.profiler.stop()
             barrier()
             ms = e0.elapsed_time(e1) / steps
             ms = max_over_ranks(ms)
@@ -284,12 +331,13 @@ def main():
                 raise RuntimeError("device status %d after the timed run" % st["status"])
             a, _ = s.get_state()
             kern = s.profile_kernels(2)
-            if form == "fp32":
+            if form == "fp32_learned":
                 live_peaks = s.alu_peaks()
             results[form] = {"ms_per_step": ms, "steps": steps, "clocks": sampler.summary(), "kernels": kern,
-                             "state": a, "workspace": s.workspace_bytes}
+                             "state": a, "workspace": s.workspace_bytes, "shapes": shapes,
+                             "smooth_fraction": st["smooth_fraction"]}
             # end to end through the C ABI with host (pinned) buffers
-            if form == "fp32":
+            if form == "fp32_learned":
                 ha = torch.empty(6 * nt, dtype=torch.float64).pin_memory()
                 hg = torch.empty(12 * nt, dtype=torch.float64).pin_memory()
                 ha.copy_(torch.from_numpy(np.ascontiguousarray(prob.avg).ravel()))
@@ -308,18 +356,35 @@ def main():
             del s
             torch.cuda.empty_cache()
 
-    P = prob.mesh.xy[prob.mesh.tri]
-    area = 0.5 * np.abs((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1]) -
-                        (P[:, 1, 1] - P[:, 0, 1]) * (P[:, 2, 0] - P[:, 0, 0]))
-    l1 = max(float(np.sum(area * np.abs(results["fp32"]["state"][v] - results["fp64"]["state"][v])) /
-                   np.sum(area * np.abs(results["fp64"]["state"][v]))) for v in (0, 3))
+    def l1_rel(p, a, b):
+        P = p.mesh.xy[p.mesh.tri]
+        area = 0.5 * np.abs((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1]) -
+                            (P[:, 1, 1] - P[:, 0, 1]) * (P[:, 2, 0] - P[:, 0, 0]))
+        return max(float(np.sum(area * np.abs(a[v] - b[v])) / np.sum(area * np.abs(b[v]))) for v in (0, 3))
 
-    r32 = results["fp32"]
-    value = ws * nt * 2 / (r32["ms_per_step"] * 1e-3)
-    value64 = ws * nt * 2 / (results["fp64"]["ms_per_step"] * 1e-3)
+    l1 = {f: l1_rel(prob, results[f]["state"], results["fp64"]["state"]) for f in ("fp32_learned", "fp32")}
+    # the stated error on a case that moves: the smooth periodic case (512
+    # triangles, 100 stages), each FP32 form against the plain FP64 GPU form
+    smooth = inputs.smooth_periodic(16)
+    with torch.cuda.stream(stream):
+        ref = solver(smooth, g.GKS2L_FP64, False)
+        ref.advance(100)
+        a64, _ = ref.get_state()
+        l1_smooth = {}
+        for form, prec, learned in forms[:2]:
+            s = solver(smooth, prec, learned)
+            s.advance(100)
+            l1_smooth[form] = l1_rel(smooth, s.get_state()[0], a64)
+            if learned:
+                l1_smooth["smooth_fraction"] = s.stats()["smooth_fraction"]
+
+    rh = results["fp32_learned"]
+    value = ws * nt * 2 / (rh["ms_per_step"] * 1e-3)
+    rates = {f: ws * nt * 2 / (results[f]["ms_per_step"] * 1e-3) for f in results}
     # roofline of the dominant kernel of the headline form
-    kern = r32["kernels"]
-    top = max(("recon", "iface", "edge", "update"), key=lambda k: kern[k])
+    kern = rh["kernels"]
+    names = ("recon", "iface", "edge", "update")
+    top = max(names, key=lambda k: kern[k])
     units = nt if top in ("recon", "update") else n_edges
     hbm = read_peaks().get("hbm_gbs", 6800.0)
     if live_peaks:
@@ -327,32 +392,36 @@ def main():
     roof = roofline("fp32", top, units, kern[top], hbm)
     tpu = TRAFFIC_PER_UNIT.get("fp32", {}).get(top)
     roof["traffic"] = tpu * units if tpu else None
-    roof["per_kernel"] = {k: round(roofline("fp32", k, nt if k in ("recon", "update") else n_edges, kern[k],
-                                             hbm)["frac"], 4) for k in ("recon", "iface", "edge", "update")}
-    share = {k: kern[k] / sum(kern[x] for x in ("recon", "iface", "edge", "update")) for k in
-             ("recon", "iface", "edge", "update")}
-    launches_per_step = 1 + 2 * 4   # step start + 4 kernels per stage
+    roof["per_kernel"] = {k: round(roofline("fp32", k, nt if k in ("recon", "gate", "update") else n_edges, kern[k],
+                                             hbm)["frac"], 4) for k in names + ("gate",)}
+    ksum = sum(kern[x] for x in names + ("gate",))
+    share = {k: kern[k] / ksum for k in names + ("gate",)}
+    launches_per_step = 1 + 2 * 5   # step start + (reconstruction, gate, interface, edge, update) per stage
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": r32["steps"],
-        "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": rh["steps"],
+        "warmup": args.warmup, "ms_per_step": rh["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64+bf16",
         "data": "synthetic (seeded jittered mesh, analytic initial data)",
         "config": {"workload": "precision/balance case: lake at rest over a Gaussian bump "
                                "b=0.5exp(-50r^2), h1+b=0.8, h2=0.2, u=0, chi=0.98, walls, jittered "
                                "%dx%d-square mesh (%d triangles), S2O4 step = 2 stages" % (args.n, args.n, nt),
-                   "form": "FP32 moments/reconstruction with FP64 balance terms and sums",
-                   "l2": "inputs larger than L2 (operators and state %.1f GB)" % (r32["workspace"] / 1e9),
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "fp64_gpu": {"value": value64, "unit": UNIT, "ms_per_step": results["fp64"]["ms_per_step"],
-                     "speedup_fp32_over_fp64": value / value64},
-        "l1_rel_fp32_vs_fp64": l1,
+                   "form": "FP32 moments/reconstruction with FP64 balance terms and sums, learned BF16 gate",
+                   "l2": "inputs larger than L2 (operators and state %.1f GB)" % (rh["workspace"] / 1e9),
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "launch_shapes": rh["shapes"]},
+        "forms": {f: {"value": rates[f], "ms_per_step": results[f]["ms_per_step"],
+                      "l1_rel_vs_fp64_gpu": l1.get(f, 0.0)} for f in results},
+        "speedup_over_fp64_gpu": value / rates["fp64"],
+        "l1_rel_smooth_case_vs_fp64_gpu": l1_smooth,
+        "gate": {"train_s": gate_train_s, "train_quality": gate_q, "smooth_fraction": rh["smooth_fraction"],
+                 "threshold": gate.THRESHOLD},
         "kernel_ms": {k: round(v, 4) for k, v in kern.items()},
         "kernel_share": {k: round(v, 4) for k, v in share.items()},
         "roofline": roof,
         "alu_peaks_tflops": live_peaks,
-        "clocks": r32["clocks"],
-        "e2e": r32["e2e"],
-        "gpu_launches": launches_per_step * r32["steps"],
+        "clocks": rh["clocks"],
+        "e2e": rh["e2e"],
+        "gpu_launches": launches_per_step * rh["steps"],
         "cpu_baseline": cpu,
     }
     if rank == 0:

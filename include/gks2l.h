@@ -213,6 +213,20 @@ int gks2l_mlp_adam(float *d_params, const float *d_grads, float *d_m, float *d_v
  * path the reconstruction uses. */
 int gks2l_mlp_forward(const float *d_X, int32_t n, const float *d_params, float *d_logits, void *stream);
 
+/* ---- launch shapes (not part of the paper) --------------------------------
+ * The interface, edge and update kernels each run in one of four launch
+ * shapes: 0: 64 threads per block, 1: 128 (default), 2: 256, 3: 128 threads
+ * held to 64 registers (eight blocks per SM). Results do not depend on them. */
+#define GKS2L_LAUNCH_SHAPES 4
+int gks2l_set_launch_shapes(gks2l_ctx *ctx, const int32_t shapes[3]);
+
+/* Autotuner: advances the state by GKS2L_LAUNCH_SHAPES * n_steps full steps,
+ * exactly as gks2l_advance would, timing the interface, edge and update
+ * kernels in each shape (CUDA events on the bound stream); keeps the fastest
+ * for each and writes them to shapes[3]. Requires a state and phase at a step
+ * boundary; returns the run's status like gks2l_advance with t_out. */
+int gks2l_autotune(gks2l_ctx *ctx, int32_t n_steps, int32_t shapes[3]);
+
 /* Kernel timing for roofline reports: advances n_steps full steps (exactly
  * like gks2l_advance, state included) but launches the stage kernels one by
  * one between CUDA events on the bound stream, then synchronises. ms[k] is

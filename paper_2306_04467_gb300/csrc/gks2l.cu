@@ -220,8 +220,12 @@ __global__ void k_harvest(Dev d, const int *perm, float tol, const float *logit_
   if (logits) logits[c] = logit_dev[j];
 }
 
+// The interface, edge and update kernels come in four launch shapes (threads
+// per block, and for one of them a register budget of eight resident blocks
+// per SM); the autotuner (gks2l_autotune) picks one per kernel. The bodies
+// are shared; the entry points differ in their launch bounds only.
 template <typename R>
-__global__ void __launch_bounds__(128) k_iface(Dev d) {
+__device__ __forceinline__ void iface_body(const Dev &d) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   int e = tid >> 2, ell = (tid >> 1) & 1, q = tid & 1;
   bool ok = e < d.ne;
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(128) k_iface(Dev d) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_edge(Dev d, Par p, int stage) {
+__device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   int e = tid >> 2, ell = (tid >> 1) & 1, q = tid & 1;
   bool ok = e < d.ne;
@@ -296,7 +300,7 @@ __device__ __forceinline__ void reduce_cell_stats(const Dev &d, bool ok, int ins
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_update(Dev d, Par p, int stage) {
+__device__ __forceinline__ void update_body(const Dev &d, const Par &p, int stage) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   bool ok = j < d.nt;
   int inst = ok ? d.inst[j] : 0;
@@ -316,6 +320,19 @@ __global__ void __launch_bounds__(128) k_update(Dev d, Par p, int stage) {
   reduce_cell_stats(d, ok, inst, ratio, m1, m2);
   if (ok && j == d.inst_first[inst]) d.t[inst] += d.dt[inst];
 }
+
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_iface(Dev d) { iface_body<R>(d); }
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_edge(Dev d, Par p, int stage) { edge_body<R>(d, p, stage); }
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_update(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
+template <typename R>
+__global__ void __launch_bounds__(128, 8) k_iface_r64(Dev d) { iface_body<R>(d); }
+template <typename R>
+__global__ void __launch_bounds__(128, 8) k_edge_r64(Dev d, Par p, int stage) { edge_body<R>(d, p, stage); }
+template <typename R>
+__global__ void __launch_bounds__(128, 8) k_update_r64(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
 
 // CFL ratio and mass of the current state (after a state is set)
 __global__ void __launch_bounds__(128) k_cfl(Dev d, Par p) {
@@ -481,6 +498,7 @@ struct gks2l_ctx {
   bool has_mlp = false;
   int n_sm = 1;                // SMs of the bound device
   cudaStream_t side = nullptr; // second stream for the gate (created with the network)
+  int shape[3] = {1, 1, 1};    // launch shapes of the interface, edge and update kernels
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int phase = 0;
   int64_t stages = 0;
@@ -678,9 +696,39 @@ void launch_recon(gks2l_ctx *c, const Par &p) {
   k_recon<R><<<blocks(d.nt, TW), dim3(TW, 6), TileLayout<R>::BYTES, c->stream>>>(d, p, c->maps);
 }
 
+// launch shapes the autotuner chooses from: 0: 64 threads, 1: 128 threads,
+// 2: 256 threads (registers as the compiler likes), 3: 128 threads held to
+// 64 registers (eight blocks per SM)
+constexpr int kShapes = 4;
+
+#define GKS2L_SHAPE_SWITCH(cfg, KERNEL, n, st, ...)                                          \
+  switch (cfg) {                                                                           \
+    case 0: KERNEL<R, 64><<<blocks(n, 64), 64, 0, st>>>(__VA_ARGS__); break;                \
+    case 2: KERNEL<R, 256><<<blocks(n, 256), 256, 0, st>>>(__VA_ARGS__); break;             \
+    case 3: KERNEL##_r64<R><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;            \
+    default: KERNEL<R, 128><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;            \
+  }
+
+template <typename R>
+void launch_iface(gks2l_ctx *c, cudaStream_t st) {
+  const size_t n = 4 * (size_t)c->d.ne;
+  GKS2L_SHAPE_SWITCH(c->shape[0], k_iface, n, st, c->d)
+}
+
+template <typename R>
+void launch_edge(gks2l_ctx *c, const Par &p, int stage, cudaStream_t st) {
+  const size_t n = 4 * (size_t)c->d.ne;
+  GKS2L_SHAPE_SWITCH(c->shape[1], k_edge, n, st, c->d, p, stage)
+}
+
+template <typename R>
+void launch_update(gks2l_ctx *c, const Par &p, int stage, cudaStream_t st) {
+  const size_t n = (size_t)c->d.nt;
+  GKS2L_SHAPE_SWITCH(c->shape[2], k_update, n, st, c->d, p, stage)
+}
+
 template <typename R>
 void launch_stage(gks2l_ctx *c, int stage) {
-  const Dev &d = c->d;
   Par p = make_par(c);
   launch_recon<R>(c, p);
   if (p.use_gate) {
@@ -691,10 +739,10 @@ void launch_stage(gks2l_ctx *c, int stage) {
     launch_gate<R>(c, p, c->side);
     cudaEventRecord(c->ev_join, c->side);
   }
-  k_iface<R><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d);
-  k_edge<R><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d, p, stage);
+  launch_iface<R>(c, c->stream);
+  launch_edge<R>(c, p, stage, c->stream);
   if (p.use_gate) cudaStreamWaitEvent(c->stream, c->ev_join, 0);
-  k_update<R><<<blocks(d.nt, 128), 128, 0, c->stream>>>(d, p, stage);
+  launch_update<R>(c, p, stage, c->stream);
 }
 
 void launch_stage_any(gks2l_ctx *c, int stage) {
@@ -1053,7 +1101,6 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[6]) {
   cudaEvent_t ev[8];
   for (int i = 0; i < 8; i++) CK(cudaEventCreate(&ev[i]));
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  const Dev &d = c->d;
   Par p = make_par(c);
   const bool f32 = c->par.precision == GKS2L_FP32;
   for (int s = 0; s < n_steps; s++) {
@@ -1070,14 +1117,14 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[6]) {
         else launch_gate<double>(c, p, c->stream);
       }
       CK(cudaEventRecord(ev[7], c->stream));
-      if (f32) k_iface<float><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d);
-      else k_iface<double><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d);
+      if (f32) launch_iface<float>(c, c->stream);
+      else launch_iface<double>(c, c->stream);
       CK(cudaEventRecord(ev[4], c->stream));
-      if (f32) k_edge<float><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d, p, stage);
-      else k_edge<double><<<blocks(4 * (size_t)d.ne, 128), 128, 0, c->stream>>>(d, p, stage);
+      if (f32) launch_edge<float>(c, p, stage, c->stream);
+      else launch_edge<double>(c, p, stage, c->stream);
       CK(cudaEventRecord(ev[5], c->stream));
-      if (f32) k_update<float><<<blocks(d.nt, 128), 128, 0, c->stream>>>(d, p, stage);
-      else k_update<double><<<blocks(d.nt, 128), 128, 0, c->stream>>>(d, p, stage);
+      if (f32) launch_update<float>(c, p, stage, c->stream);
+      else launch_update<double>(c, p, stage, c->stream);
       CK(cudaEventRecord(ev[6], c->stream));
       CK(cudaEventSynchronize(ev[6]));
       float t;
@@ -1103,6 +1150,37 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[6]) {
   ms[5] = acc[5] / (2.0 * n_steps);
   c->stages += 2 * n_steps;
   return GKS2L_OK;
+}
+
+int gks2l_set_launch_shapes(gks2l_ctx *c, const int32_t shapes[3]) {
+  if (!c || !shapes) return GKS2L_EINVAL;
+  for (int k = 0; k < 3; k++)
+    if (shapes[k] < 0 || shapes[k] >= kShapes) return GKS2L_EINVAL;
+  for (int k = 0; k < 3; k++) c->shape[k] = shapes[k];
+  drop_graph(c);
+  return GKS2L_OK;
+}
+
+int gks2l_autotune(gks2l_ctx *c, int32_t n_steps, int32_t shapes[3]) {
+  if (!c || !shapes || n_steps <= 0) return GKS2L_EINVAL;
+  if (!c->bound || !c->has_state || c->phase != 0) return GKS2L_ESTATE;
+  double best[3] = {INFINITY, INFINITY, INFINITY};
+  int pick[3] = {c->shape[0], c->shape[1], c->shape[2]};
+  for (int b = 0; b < kShapes; b++) {
+    for (int k = 0; k < 3; k++) c->shape[k] = b;
+    double ms[6];
+    int rc = gks2l_profile_kernels(c, n_steps, ms);
+    if (rc) return rc;
+    // ms: reconstruction, interface, edge, update, ...
+    for (int k = 0; k < 3; k++)
+      if (ms[1 + k] < best[k]) {
+        best[k] = ms[1 + k];
+        pick[k] = b;
+      }
+  }
+  for (int k = 0; k < 3; k++) c->shape[k] = shapes[k] = pick[k];
+  drop_graph(c);
+  return check_status(c);
 }
 
 int gks2l_alu_peaks(gks2l_ctx *c, double tflops[2]) {

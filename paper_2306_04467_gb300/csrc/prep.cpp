@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <thread>
 #include <unordered_map>
 
 namespace gks2l {
@@ -243,8 +244,7 @@ int prepare(int n, const gks2l_mesh *meshes, Prep &out, std::string &err) {
     for (int t = 0; t < M.n_tri; t++) {
       uint32_t qx = (uint32_t)std::min(4294967295.0, std::floor((loc[t].cx - bx0) / sx * 4294967295.0));
       uint32_t qy = (uint32_t)std::min(4294967295.0, std::floor((loc[t].cy - by0) / sy * 4294967295.0));
-      key[t] = (spread_bits(qx >> 0) & 0xFFFFFFFFFFFFFFFFull) | (spread_bits(qy) << 1);
-      // spread_bits takes 32 bits but keeps 32 interleaved positions
+      // Morton key of the top 16 bits of each quantised centroid coordinate
       key[t] = spread_bits(qx >> 16) | (spread_bits(qy >> 16) << 1);
     }
     std::vector<int> order(M.n_tri);
@@ -417,6 +417,10 @@ int prepare(int n, const gks2l_mesh *meshes, Prep &out, std::string &err) {
   P.plane.assign(6 * nt, 0.0);
   P.cedge.assign(3 * nt, 0);
   const TriRule &rule = tri_rule();
+  // first pass (serial: it registers image transforms): geometry and the
+  // compact stencil of every cell
+  std::vector<Img> lists((size_t)kSlots * nt);
+  std::vector<int> nlist(nt);
   for (int j = 0; j < nt; j++) {
     const Cell &C = cells[j];
     P.area[j] = C.area;
@@ -460,7 +464,16 @@ int prepare(int n, const gks2l_mesh *meshes, Prep &out, std::string &err) {
       int code = xf_code(list[s].T);
       if (code < 0) { err = "too many distinct image transforms"; return GKS2L_EMESH; }
       P.st_xf[s * nt + j] = (int8_t)code;
+      lists[(size_t)kSlots * j + s] = list[s];
     }
+    nlist[j] = na;
+  }
+  // second pass (threads over cell ranges): the per-cell operators
+  auto ops = [&](int j0, int j1, std::string &terr) {
+  for (int j = j0; j < j1; j++) {
+    const Cell &C = cells[j];
+    const Img *list = &lists[(size_t)kSlots * j];
+    const int na = nlist[j];
     // LS system: averages of the zero-mean basis over the stencil images,
     // then h-scaled average derivatives over the cell and its faces
     double am[10], ax[10], ay[10];
@@ -484,7 +497,7 @@ int prepare(int n, const gks2l_mesh *meshes, Prep &out, std::string &err) {
         A[(na + 2 * f + 1) * kCoef + k - 1] = iy[k];
       }
     }
-    if (!pinv_mgs(m, kCoef, A.data(), Pm.data())) { err = "singular least-squares system"; return GKS2L_EMESH; }
+    if (!pinv_mgs(m, kCoef, A.data(), Pm.data())) { terr = "singular least-squares system"; return; }
     for (int r = 0; r < kCoef; r++) {
       for (int s = 0; s < na; s++) P.lsq[(r * kCols + s) * nt + j] = Pm[r * m + s];
       for (int c = 0; c < 8; c++) P.lsq[(r * kCols + 9 + c) * nt + j] = Pm[r * m + na + c];
@@ -495,7 +508,7 @@ int prepare(int n, const gks2l_mesh *meshes, Prep &out, std::string &err) {
       image_tri(cells, list[f], T);
       tri_avg(C, T, im, ix, iy);
       double B5[10] = {im[1] - am[1], im[2] - am[2], 1, 0, 0, 1, 1, 0, 0, 1}, P5[10];
-      if (!pinv_mgs(5, 2, B5, P5)) { err = "singular P1 system"; return GKS2L_EMESH; }
+      if (!pinv_mgs(5, 2, B5, P5)) { terr = "singular P1 system"; return; }
       for (int q = 0; q < 10; q++) P.p1op[(f * 10 + q) * nt + j] = P5[q];
     }
     // smoothness form: mean over the cell of squared xi-derivatives of
@@ -541,6 +554,16 @@ int prepare(int n, const gks2l_mesh *meshes, Prep &out, std::string &err) {
       P.plane[(2 * 2 + d) * nt + j] = c2[d];
     }
   }
+  };
+  const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  const int chunk = (nt + nth - 1) / nth;
+  std::vector<std::string> terrs(nth);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nth && t * chunk < nt; t++)
+    pool.emplace_back(ops, t * chunk, std::min(nt, (t + 1) * chunk), std::ref(terrs[t]));
+  for (auto &th : pool) th.join();
+  for (auto &e : terrs)
+    if (!e.empty()) { err = e; return GKS2L_EMESH; }
   out = std::move(P);
   return GKS2L_OK;
 }

@@ -62,6 +62,8 @@ SIGNATURES = {
     "gks2l_get_state_device": (_I, [_P, _P, _P]),
     "gks2l_stats": (_I, [_P, ctypes.POINTER(gks2l_stats_t)]),
     "gks2l_profile_kernels": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double * 6)]),
+    "gks2l_set_launch_shapes": (_I, [_P, ctypes.POINTER(ctypes.c_int32 * 3)]),
+    "gks2l_autotune": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32 * 3)]),
     "gks2l_alu_peaks": (_I, [_P, ctypes.POINTER(ctypes.c_double * 2)]),
     "gks2l_set_mlp": (_I, [_P, _P, ctypes.c_size_t]),
     "gks2l_harvest": (_I, [_P, ctypes.c_float, _P, _P, _P]),
@@ -218,6 +220,18 @@ class Solver:
         ms = (ctypes.c_double * 6)()
         _check(load().gks2l_profile_kernels(self._h, int(n_steps), ctypes.byref(ms)), "gks2l_profile_kernels")
         return {"recon": ms[0], "iface": ms[1], "edge": ms[2], "update": ms[3], "step_begin": ms[4], "gate": ms[5]}
+
+    def set_launch_shapes(self, shapes):
+        """Launch shapes (0..3) of the interface, edge and update kernels."""
+        b = (ctypes.c_int32 * 3)(*[int(x) for x in shapes])
+        _check(load().gks2l_set_launch_shapes(self._h, ctypes.byref(b)), "gks2l_set_launch_shapes")
+
+    def autotune(self, n_steps=2):
+        """Time each launch shape for n_steps steps (they advance the state);
+        keep the fastest per kernel and return the choices."""
+        b = (ctypes.c_int32 * 3)()
+        _check(load().gks2l_autotune(self._h, int(n_steps), ctypes.byref(b)), "gks2l_autotune")
+        return list(b)
 
     def alu_peaks(self):
         """Measured FP32 and FP64 FMA throughput of the device, TFLOP/s."""
