@@ -52,6 +52,7 @@ template <typename R> struct TileLayout {
   static constexpr unsigned SX = ST + kSlots * TW * 4;
   static constexpr unsigned BAR = SX + 384;                   // 9 * 32 int8 rounded to 128 B
   static constexpr unsigned BYTES = BAR + 16;
+  static_assert(2 * TW * (NREC + 1) * sizeof(R) <= P1 - LSQ, "side-record staging fits in the LSQ rows");
   static constexpr unsigned TX = BAR - 96;                    // bytes the six copies deliver
   static constexpr unsigned TX_LINEAR = TX - (MM - P1);       // without the P1 and beta rows
 };
@@ -152,7 +153,33 @@ __global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p,
       atomicAdd(&d.gate_count[1], (unsigned long long)nc);
     }
   }
-  if (active) recon_unit<R>(d, p, o, j, v, linear);
+  R rhs[NCOL], a[9];
+  if (active) {
+    recon_gather<R>(d, o, j, v, rhs);
+    recon_p3<R>(o, rhs, a);
+  }
+  // every warp is done with the LSQ rows: their space stages the side records
+  __syncthreads();
+  R *stg = (R *)(sm + T::LSQ);
+  if (active) recon_finish<R>(d, p, o, j, v, rhs, a, linear, stg);
+  if (v == 5 && j < d.nt) {
+    // the constant words: 1/h_s and the bottom slope
+    R *r0 = stg + (size_t)threadIdx.x * (NREC + 1), *r1 = stg + (size_t)(TW + threadIdx.x) * (NREC + 1);
+    const R ih = ((const R *)d.ihsR)[j];
+    r0[11] = ih;
+    r1[11] = ih;
+    r0[23] = ((const R *)d.bgR)[j];
+    r0[35] = ((const R *)d.bgR)[d.cs + j];
+    r1[23] = r1[35] = 0;
+  }
+  __syncthreads();
+  // coalesced write-out: each layer's records of the tile are contiguous
+  const int tid = threadIdx.y * TW + threadIdx.x;
+  for (int i = tid; i < 2 * TW * NREC; i += TW * 6) {
+    const int lay = i / (TW * NREC), r = i - lay * TW * NREC, cell = r / NREC, w = r - cell * NREC;
+    if (j0 + cell < d.nt)
+      ((R *)d.srec)[((size_t)lay * d.cs + j0) * NREC + r] = stg[(lay * TW + cell) * (NREC + 1) + w];
+  }
 }
 
 // Troubled-cell gate (not part of the paper). It runs on a second stream
@@ -545,7 +572,7 @@ size_t layout(gks2l_ctx *c, char *base) {
   d.Wn = k.take<double>(6 * cs);
   d.Ln = k.take<double>(6 * cs);
   d.Ltn = k.take<double>(6 * cs);
-  d.coef = k.take<char>(rs * 60 * cs);
+  d.srec = k.take<char>(rs * 2 * NREC * cs);
   d.omg = k.take<char>(rs * 2 * cs);
   d.mlp = k.take<MlpDev>(1);
   d.gate_mask = k.take<unsigned>(cs / TW);
@@ -613,6 +640,8 @@ int upload_form(gks2l_ctx *c, const void *dst, const std::vector<double> &src, i
   return upload(c, dst, src);
 }
 
+inline unsigned blocks(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
+
 int upload_bathymetry(gks2l_ctx *c) {
   std::vector<double> bm, bx, by, e0, e1;
   bathymetry(c->prep, c->has_b ? c->bvert.data() : nullptr, bm, bx, by, e0, e1);
@@ -642,7 +671,6 @@ Par make_par(const gks2l_ctx *c) {
   return p;
 }
 
-inline unsigned blocks(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
 // tensor maps of the per-cell operator rows ([rows][cs], tiles of TW cells)
 int make_maps(gks2l_ctx *c) {

@@ -21,6 +21,7 @@
 #pragma once
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #ifndef __CUDACC__
 #define __host__
@@ -38,6 +39,13 @@ constexpr int NV = 6;        // h2, h2U2, h2V2, h1 (as eta1 = h1 + B), h1U1, h1V
 constexpr int NSLOT = 9;
 constexpr int NCOL = 17;
 constexpr int NCOEF = 10;    // per variable: c0 (value offset) + 9 Taylor coefficients
+// Side record of one cell for one layer: three slots of 12 values, one per
+// variable of the layer (level, x- and y-discharge), each the 10 deviation
+// coefficients, the cell-average deviation, then a constant: 1/h_s in slot 0,
+// the bottom slope in slots 1-2 (lower layer; zero in the upper). An edge
+// point reads its layer's record and slot 0 (the level) of the other layer's.
+// 16-byte aligned, read with vector loads.
+constexpr int NREC = 36;
 
 // Device view of the workspace. R-typed arrays are stored as void* and cast.
 struct Dev {
@@ -61,7 +69,7 @@ struct Dev {
   void *dq, *dg;            // deviation mirrors [6][cell], gradients [12][cell], type R
   void *hrefc;              // R1 - B_j per cell, type R
   double *Wn, *Ln, *Ltn;    // stage snapshot (FP64)
-  void *coef;               // reconstruction deviations [v*10+k][cell], type R
+  void *srec;               // side records [layer][cell][NREC], type R (lower layer first)
   void *omg;                // omega_H / gamma_H of eta1 [0] and h2 [1], type R
   const void *mlp;          // gate network, packed image (MlpDev)
   unsigned *gate_mask;      // per tile of 32 cells: bit i = cell i takes the linear weights
@@ -118,6 +126,19 @@ template <typename R> __host__ __device__ __forceinline__ R r_sqrt(R x);
 template <> __host__ __device__ __forceinline__ double r_sqrt<double>(double x) { return sqrt(x); }
 template <> __host__ __device__ __forceinline__ float r_sqrt<float>(float x) { return sqrtf(x); }
 template <typename R> __host__ __device__ __forceinline__ R r_abs(R x) { return x < 0 ? -x : x; }
+
+// the bits of a double as a signed integer (> 0: positive, nonzero, and
+// finite or NaN), and a finiteness test on them
+__host__ __device__ __forceinline__ long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(x);
+#else
+  long long b;
+  std::memcpy(&b, &x, sizeof b);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ bool finite_bits(double x) { return ((dbits(x) >> 52) & 0x7ff) != 0x7ff; }
 
 template <typename R>
 __host__ __device__ __forceinline__ void monos(R x, R y, R m[10], R mx[10], R my[10]) {
@@ -237,11 +258,13 @@ __host__ __device__ inline void recon_p3(const CellOps<R> &o, const R rhs[NCOL],
   }
 }
 
+// The result goes to the cell's side records: straight to global memory, or,
+// with `stage` set, to a block's staging tile [layer][cell in tile][NREC + 1]
+// (o.stride cells per layer) that the block then writes out coalesced.
 template <typename R>
 __host__ __device__ inline void recon_finish(const Dev &d, const Par &p, const CellOps<R> &o, int j, int v,
-                                             const R rhs[NCOL], const R a[9], bool linear) {
+                                             const R rhs[NCOL], const R a[9], bool linear, R *stage = nullptr) {
   const int N = d.cs, S = o.stride, I = o.idx;
-  R *coef = (R *)d.coef;
   const R q0 = ((const R *)d.dq)[v * N + j];
   const R gh = pv<R>(p.gam_hi, p.gam_hif), gl = ((R)1 - gh) * (R)(1.0 / 3.0);
   R fac = 1, wf[3] = {gl, gl, gl}, b[3][2] = {{0, 0}, {0, 0}, {0, 0}};
@@ -300,7 +323,14 @@ __host__ __device__ inline void recon_finish(const Dev &d, const Par &p, const C
   R c0 = 0;
   for (int k = 3; k < 10; k++) c0 -= r[k] * o.mm[(k - 3) * S + I];
   r[0] = c0;
-  for (int k = 0; k < 10; k++) coef[(v * NCOEF + k) * N + j] = r[k];
+  // the layer's side record (vars 3,4,5 -> lower, 0,1,2 -> upper), and the
+  // other layer's record for the level variables 0 and 3
+  R *rec = stage ? stage : (R *)d.srec;
+  const size_t ncell = stage ? (size_t)S : (size_t)N, cell = stage ? (size_t)I : (size_t)j;
+  const int rs = stage ? NREC + 1 : NREC;
+  R *p0 = rec + ((size_t)(v >= 3 ? 0 : 1) * ncell + cell) * rs + (v % 3) * 12;
+  for (int k = 0; k < 10; k++) p0[k] = r[k];
+  p0[10] = q0;
   if (v == 3) ((R *)d.omg)[j] = fac;
   if (v == 0) ((R *)d.omg)[N + j] = fac;
 }
@@ -312,6 +342,14 @@ __host__ __device__ inline void recon_unit(const Dev &d, const Par &p, const Cel
   recon_gather<R>(d, o, j, v, rhs);
   recon_p3<R>(o, rhs, a);
   recon_finish<R>(d, p, o, j, v, rhs, a, linear);
+  if (v == 5) {
+    // the side records' constant words: 1/h_s and the bottom slope
+    R *r0 = (R *)d.srec + (size_t)j * NREC, *r1 = (R *)d.srec + ((size_t)d.cs + j) * NREC;
+    r0[11] = r1[11] = ((const R *)d.ihsR)[j];
+    r0[23] = ((const R *)d.bgR)[j];
+    r0[35] = ((const R *)d.bgR)[d.cs + j];
+    r1[23] = r1[35] = 0;
+  }
 }
 
 // ------------------------------------------------- evaluation at an edge point
@@ -329,21 +367,60 @@ template <typename R> struct SideVals {
 
 // cell c's reconstruction at scaled point (x, y), seen through transform xf;
 // href is the depth of the reference level at the point
+// n consecutive values of a side record (n a multiple of 4)
+template <typename R, int n> __host__ __device__ __forceinline__ void load_rec(const R *p, R *w) {
+  for (int k = 0; k < n; k++) w[k] = p[k];
+}
+#ifdef __CUDACC__
+template <> __device__ __forceinline__ void load_rec<float, NREC>(const float *p, float *w) {
+  const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+  for (int k = 0; k < NREC / 4; k++) {
+    float4 t = q[k];
+    w[4 * k] = t.x; w[4 * k + 1] = t.y; w[4 * k + 2] = t.z; w[4 * k + 3] = t.w;
+  }
+}
+template <> __device__ __forceinline__ void load_rec<float, 12>(const float *p, float *w) {
+  const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    float4 t = q[k];
+    w[4 * k] = t.x; w[4 * k + 1] = t.y; w[4 * k + 2] = t.z; w[4 * k + 3] = t.w;
+  }
+}
+template <> __device__ __forceinline__ void load_rec<double, NREC>(const double *p, double *w) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+  for (int k = 0; k < NREC / 2; k++) {
+    double2 t = q[k];
+    w[2 * k] = t.x; w[2 * k + 1] = t.y;
+  }
+}
+template <> __device__ __forceinline__ void load_rec<double, 12>(const double *p, double *w) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    double2 t = q[k];
+    w[2 * k] = t.x; w[2 * k + 1] = t.y;
+  }
+}
+#endif
+
 template <typename R>
 __host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, R x, R y, R href, SideVals<R> &s) {
   const int N = d.cs;
-  const R *coef = (const R *)d.coef;
-  const R *dq = (const R *)d.dq;
-  const int v0 = ell == 0 ? 3 : 0, vo = ell == 0 ? 0 : 3;
+  R w[NREC], wo[12];
+  load_rec<R, NREC>((const R *)d.srec + ((size_t)ell * N + c) * NREC, w);
+  load_rec<R, 12>((const R *)d.srec + ((size_t)(1 - ell) * N + c) * NREC, wo);
   R m[10], mx[10], my[10];
   monos<R>(x, y, m, mx, my);
-  const R ih = ((const R *)d.ihsR)[c];
+  const R ih = w[11];
   R dev[3], gx[4], gy[4];
   for (int i = 0; i < 4; i++) {
-    int v = i < 3 ? v0 + i : vo;
+    const R *cf = i < 3 ? w + 12 * i : wo;
     R a = 0, ax = 0, ay = 0;
     for (int k = 0; k < 10; k++) {
-      R ck = coef[(v * NCOEF + k) * N + c];
+      R ck = cf[k];
       a += ck * m[k];
       ax += ck * mx[k];
       ay += ck * my[k];
@@ -352,16 +429,16 @@ __host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, 
     gx[i] = ax * ih;
     gy[i] = ay * ih;
   }
-  s.d = dq[v0 * N + c] + dev[0];
+  s.d = w[10] + dev[0];
   s.h = href + s.d;
-  s.mx = dq[(v0 + 1) * N + c] + dev[1];
-  s.my = dq[(v0 + 2) * N + c] + dev[2];
+  s.mx = w[22] + dev[1];
+  s.my = w[34] + dev[2];
   s.glev[0] = gx[0]; s.glev[1] = gy[0];
   s.gm[0][0] = gx[1]; s.gm[0][1] = gy[1];
   s.gm[1][0] = gx[2]; s.gm[1][1] = gy[2];
   s.goth[0] = gx[3]; s.goth[1] = gy[3];
   R gb[2] = {0, 0};
-  if (ell == 0) { gb[0] = ((const R *)d.bgR)[c]; gb[1] = ((const R *)d.bgR)[N + c]; }
+  if (ell == 0) { gb[0] = w[23]; gb[1] = w[35]; }
   if (xf != 0) {
     const double *M = d.xf + 4 * xf;
     R mv[2] = {s.mx, s.my};
@@ -749,10 +826,11 @@ __host__ __device__ inline double update_unit(const Dev &d, const Par &p, int j,
   dqw[j] = (R)(nw[0] - d.ref[2 * in]);
   dqw[3 * N + j] = (R)((nw[3] + d.bmean[j]) - d.ref[2 * in + 1]);
   for (int i = 0; i < 4; i++) dqw[mom[i] * N + j] = (R)nw[mom[i]];
+  // health flags by integer tests on the bits (off the FP64 pipe)
   int fl = 0;
   for (int v = 0; v < NV; v++)
-    if (!isfinite(nw[v]) || !isfinite(GGn[v][0]) || !isfinite(GGn[v][1])) fl |= 2;
-  if (!(nw[0] > 0) || !(nw[3] > 0)) fl |= 1;
+    if (!finite_bits(nw[v]) || !isfinite(GGn[v][0]) || !isfinite(GGn[v][1])) fl |= 2;
+  if (!(dbits(nw[0]) > 0) || !(dbits(nw[3]) > 0)) fl |= 1;
   *flags = fl;
   if (stage != 2) return 0;
   R um = 0;
