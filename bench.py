@@ -47,15 +47,15 @@ N_SQ = 1024
 # unit; the FP32-form reconstruction count is the gated one on this workload
 # (every tile smooth). Bytes are the minimum one launch must move with the
 # structure-of-arrays layout, each cell or edge record read or written once
-# (reconstruction: operators 9x17 + 7 + stencil 9 + gathers + 60 coefficients
-# out, without the P1 and smoothness rows for gated tiles; gate: 3 neighbour
-# ids and transforms, eta1/h2 values and gradients, scales; interface: edge
-# geometry, both cells' coefficients, two levels out; edge: the same plus
-# plane rows and blend weights, 24 interface values out; update: three edges'
-# fluxes and interface values, state in/out with the S2O4 snapshot, mirrors
-# out). Units: cells for recon, gate and update, edges for iface and edge.
+# (reconstruction: operators 9x17 + 7 + stencil 9 + gathers + two 36-value
+# side records out, without the P1 and smoothness rows for gated tiles; gate:
+# 3 neighbour ids and transforms, eta1/h2 values and gradients, scales;
+# interface: edge geometry, both cells' side records, two levels out; edge:
+# the same plus plane rows and blend weights, 24 interface values out;
+# update: three edges' fluxes and interface values, state in/out with the
+# S2O4 snapshot, mirrors out). Units: cells for recon, gate and update, edges for iface and edge.
 WORK_PER_UNIT = {
-    "fp32": {"recon": (2195, 0, 1017), "gate": (280, 0, 51), "iface": (930, 0, 244), "edge": (6981, 0, 366),
+    "fp32": {"recon": (2195, 0, 1069), "gate": (280, 0, 51), "iface": (930, 0, 265), "edge": (6981, 0, 374),
              "update": (331, 73, 570)},
     "fp64": {"recon": (69, 4593, 2209), "gate": (280, 0, 63), "iface": (15, 1349, 473), "edge": (107, 9162, 696),
              "update": (0, 343, 850)},
