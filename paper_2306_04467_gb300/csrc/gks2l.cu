@@ -52,7 +52,7 @@ template <typename R> struct TileLayout {
   static constexpr unsigned SX = ST + kSlots * TW * 4;
   static constexpr unsigned BAR = SX + 384;                   // 9 * 32 int8 rounded to 128 B
   static constexpr unsigned BYTES = BAR + 16;
-  static_assert(2 * TW * (NREC + 1) * sizeof(R) <= P1 - LSQ, "side-record staging fits in the LSQ rows");
+  static_assert(2 * TW * NREC * sizeof(R) <= P1 - LSQ, "side-record staging fits in the LSQ rows");
   static constexpr unsigned TX = BAR - 96;                    // bytes the six copies deliver
   static constexpr unsigned TX_LINEAR = TX - (MM - P1);       // without the P1 and beta rows
 };
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p,
   if (active) recon_finish<R>(d, p, o, j, v, rhs, a, linear, stg);
   if (v == 5 && j < d.nt) {
     // the constant words: 1/h_s and the bottom slope
-    R *r0 = stg + (size_t)threadIdx.x * (NREC + 1), *r1 = stg + (size_t)(TW + threadIdx.x) * (NREC + 1);
+    R *r0 = stg + (size_t)threadIdx.x * NREC, *r1 = stg + (size_t)(TW + threadIdx.x) * NREC;
     const R ih = ((const R *)d.ihsR)[j];
     r0[11] = ih;
     r1[11] = ih;
@@ -173,12 +173,17 @@ __global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p,
     r1[23] = r1[35] = 0;
   }
   __syncthreads();
-  // coalesced write-out: each layer's records of the tile are contiguous
+  // coalesced write-out: each layer's records of the tile are contiguous, and
+  // so is the staging tile, so the copy moves 16-byte vectors
+  constexpr int V = 16 / sizeof(R);                 // values per vector
+  constexpr int NV_LAYER = TW * NREC / V;           // vectors per layer
   const int tid = threadIdx.y * TW + threadIdx.x;
-  for (int i = tid; i < 2 * TW * NREC; i += TW * 6) {
-    const int lay = i / (TW * NREC), r = i - lay * TW * NREC, cell = r / NREC, w = r - cell * NREC;
-    if (j0 + cell < d.nt)
-      ((R *)d.srec)[((size_t)lay * d.cs + j0) * NREC + r] = stg[(lay * TW + cell) * (NREC + 1) + w];
+  const int ncell = min(TW, d.nt - j0);             // the last tile may be partial
+  for (int i = tid; i < 2 * NV_LAYER; i += TW * 6) {
+    const int lay = i / NV_LAYER, r = i - lay * NV_LAYER;
+    if (r * V < ncell * NREC)
+      reinterpret_cast<uint4 *>((R *)d.srec + ((size_t)lay * d.cs + j0) * NREC)[r] =
+          reinterpret_cast<const uint4 *>(stg + lay * TW * NREC)[r];
   }
 }
 

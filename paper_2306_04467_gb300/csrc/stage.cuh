@@ -259,8 +259,9 @@ __host__ __device__ inline void recon_p3(const CellOps<R> &o, const R rhs[NCOL],
 }
 
 // The result goes to the cell's side records: straight to global memory, or,
-// with `stage` set, to a block's staging tile [layer][cell in tile][NREC + 1]
-// (o.stride cells per layer) that the block then writes out coalesced.
+// with `stage` set, to a block's staging tile [layer][cell in tile][NREC]
+// (o.stride cells per layer) that the block then writes out with 16-byte
+// stores.
 template <typename R>
 __host__ __device__ inline void recon_finish(const Dev &d, const Par &p, const CellOps<R> &o, int j, int v,
                                              const R rhs[NCOL], const R a[9], bool linear, R *stage = nullptr) {
@@ -327,7 +328,7 @@ __host__ __device__ inline void recon_finish(const Dev &d, const Par &p, const C
   // other layer's record for the level variables 0 and 3
   R *rec = stage ? stage : (R *)d.srec;
   const size_t ncell = stage ? (size_t)S : (size_t)N, cell = stage ? (size_t)I : (size_t)j;
-  const int rs = stage ? NREC + 1 : NREC;
+  const int rs = NREC;
   R *p0 = rec + ((size_t)(v >= 3 ? 0 : 1) * ncell + cell) * rs + (v % 3) * 12;
   for (int k = 0; k < 10; k++) p0[k] = r[k];
   p0[10] = q0;

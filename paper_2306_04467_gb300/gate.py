@@ -6,10 +6,12 @@ blends a P3 least-squares polynomial with three P1 candidates through WENO-Z
 weights; where the data are smooth those weights stay at the linear ones and
 the result is the P3 polynomial. The gate, a 24 -> 32 -> 32 -> 1 MLP, predicts
 that from the cell's and its face neighbours' averages and gradients. It runs
-inside the reconstruction on the data that kernel gathers anyway and decides
-for the next stage: cells it calls smooth skip the smoothness indicators and
-weights there, and a tile of 32 such cells skips loading their operators. Labels are the method's own: a cell is troubled when any of its
-WENO weights departs from the linear one by more than `tol` (relative).
+as its own kernel on a second stream beside a stage's interface and edge
+kernels and decides for the next stage: cells it calls smooth skip the
+smoothness indicators and weights there, and a tile of 32 such cells skips
+loading their operators. Labels are the method's own: a cell is troubled when
+any of its WENO weights departs from the linear one by more than `tol`
+(relative).
 
 Everything numeric here runs in the library (gks2l_harvest, gks2l_mlp_grad,
 gks2l_mlp_adam, gks2l_mlp_forward); PyTorch holds device memory.
