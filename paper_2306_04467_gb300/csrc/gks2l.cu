@@ -300,9 +300,15 @@ __device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage)
   }
 }
 
+// min over the warp of non-negative doubles (or +inf): their bit patterns
+// order like the values, so the comparison runs on the integer pipes
 __device__ __forceinline__ double warp_min(double v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(FULL, v, o));
-  return v;
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long u = __shfl_xor_sync(FULL, b, o);
+    b = u < b ? u : b;
+  }
+  return __longlong_as_double((long long)b);
 }
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
