@@ -98,7 +98,8 @@ typedef struct {
 
 /* Run statistics (FP64 sums taken on the device). */
 typedef struct {
-  double mass[2];        /* sum |Omega_j| h_j for layer 1 (lower) and layer 2  */
+  double mass[2];        /* sum |Omega_j| h_j of the current state (summed when
+                            the statistics are read), layer 1 (lower), layer 2 */
   double t;              /* simulated time of instance 0                        */
   double dt_last;        /* last step size of instance 0                        */
   int64_t stages_done;

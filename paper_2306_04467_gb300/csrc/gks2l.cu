@@ -315,23 +315,37 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// min of dX/U_max and per-layer mass, reduced per warp when the warp lies in
-// one instance (the usual case), per lane otherwise
-__device__ __forceinline__ void reduce_cell_stats(const Dev &d, bool ok, int inst, double ratio, double m1,
-                                                  double m2) {
+// min of dX/U_max per instance, reduced per warp when the warp lies in one
+// instance (the usual case), per lane otherwise
+__device__ __forceinline__ void reduce_cfl(const Dev &d, bool ok, int inst, double ratio) {
   int lane = threadIdx.x & 31;
   int i0 = __shfl_sync(FULL, inst, 0);
   bool uniform = __all_sync(FULL, !ok || inst == i0) && __shfl_sync(FULL, ok ? 1 : 0, 0);
   if (uniform) {
     double r = warp_min(ok ? ratio : INFINITY);
-    double s1 = warp_sum(ok ? m1 : 0.0), s2 = warp_sum(ok ? m2 : 0.0);
+    if (lane == 0 && r < INFINITY) atomicMin(&d.dtbits[i0], (unsigned long long)__double_as_longlong(r));
+  } else if (ok && ratio < INFINITY) {
+    atomicMin(&d.dtbits[inst], (unsigned long long)__double_as_longlong(ratio));
+  }
+}
+
+// per-layer masses of the current state, per instance (FP64 sums; taken when
+// the statistics are read, not in the stage kernels)
+__global__ void k_mass(Dev d) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  bool ok = j < d.nt;
+  int inst = ok ? d.inst[j] : 0;
+  double m1 = ok ? d.area[j] * d.avg[3 * d.cs + j] : 0.0, m2 = ok ? d.area[j] * d.avg[j] : 0.0;
+  int lane = threadIdx.x & 31;
+  int i0 = __shfl_sync(FULL, inst, 0);
+  bool uniform = __all_sync(FULL, !ok || inst == i0) && __shfl_sync(FULL, ok ? 1 : 0, 0);
+  if (uniform) {
+    double s1 = warp_sum(m1), s2 = warp_sum(m2);
     if (lane == 0) {
-      if (r < INFINITY) atomicMin(&d.dtbits[i0], (unsigned long long)__double_as_longlong(r));
       atomicAdd(&d.mass[2 * i0], s1);
       atomicAdd(&d.mass[2 * i0 + 1], s2);
     }
   } else if (ok) {
-    if (ratio < INFINITY) atomicMin(&d.dtbits[inst], (unsigned long long)__double_as_longlong(ratio));
     atomicAdd(&d.mass[2 * inst], m1);
     atomicAdd(&d.mass[2 * inst + 1], m2);
   }
@@ -350,12 +364,7 @@ __device__ __forceinline__ void update_body(const Dev &d, const Par &p, int stag
   }
   if (fl) atomicOr(d.status, fl);
   if (stage != 2) return;
-  double m1 = 0, m2 = 0;
-  if (ok) {
-    m1 = d.area[j] * d.avg[3 * d.cs + j];
-    m2 = d.area[j] * d.avg[j];
-  }
-  reduce_cell_stats(d, ok, inst, ratio, m1, m2);
+  reduce_cfl(d, ok, inst, ratio);
   if (ok && j == d.inst_first[inst]) d.t[inst] += d.dt[inst];
 }
 
@@ -372,12 +381,12 @@ __global__ void __launch_bounds__(128, 8) k_edge_r64(Dev d, Par p, int stage) { 
 template <typename R>
 __global__ void __launch_bounds__(128, 8) k_update_r64(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
 
-// CFL ratio and mass of the current state (after a state is set)
+// CFL ratio of the current state (after a state is set)
 __global__ void __launch_bounds__(128) k_cfl(Dev d, Par p) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   bool ok = j < d.nt;
   int inst = ok ? d.inst[j] : 0;
-  double ratio = INFINITY, m1 = 0, m2 = 0;
+  double ratio = INFINITY;
   if (ok) {
     double um = 0;
     for (int l = 0; l < 2; l++) {
@@ -391,17 +400,14 @@ __global__ void __launch_bounds__(128) k_cfl(Dev d, Par p) {
       atomicOr(d.status, 2);
       ratio = INFINITY;
     }
-    m1 = d.area[j] * d.avg[3 * d.cs + j];
-    m2 = d.area[j] * d.avg[j];
   }
-  reduce_cell_stats(d, ok, inst, ratio, m1, m2);
+  reduce_cfl(d, ok, inst, ratio);
 }
 
 __global__ void k_reset_stats(Dev d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.ninst) return;
   d.dtbits[i] = DBL_INF_BITS;
-  d.mass[2 * i] = d.mass[2 * i + 1] = 0;
 }
 
 // step size of each instance from the CFL ratio of the current state (Sec. 4),
@@ -425,7 +431,6 @@ __global__ void k_step_begin(Dev d, Par p, const double *tend) {
   d.dt[i] = dt;
   ((R *)d.dtR)[i] = (R)dt;
   d.dtbits[i] = DBL_INF_BITS;
-  d.mass[2 * i] = d.mass[2 * i + 1] = 0;
 }
 
 // deviation mirrors of a freshly set state: dq, dg (gradients given in the
@@ -1112,6 +1117,9 @@ int gks2l_stats(gks2l_ctx *c, gks2l_stats_t *out) {
   double t = 0, dt = 0;
   int st = 0;
   unsigned long long cnt[2] = {0, 0};
+  CK(cudaMemsetAsync(c->d.mass, 0, mass.size() * sizeof(double), c->stream));
+  k_mass<<<blocks(c->prep.nt, 128), 128, 0, c->stream>>>(c->d);
+  CK(cudaGetLastError());
   CK(cudaMemcpyAsync(mass.data(), c->d.mass, mass.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(&t, c->d.t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(&dt, c->d.dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
