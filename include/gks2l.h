@@ -215,10 +215,11 @@ int gks2l_mlp_adam(float *d_params, const float *d_grads, float *d_m, float *d_v
 int gks2l_mlp_forward(const float *d_X, int32_t n, const float *d_params, float *d_logits, void *stream);
 
 /* ---- launch shapes (not part of the paper) --------------------------------
- * The interface, edge and update kernels each run in one of four launch
+ * The interface, edge and update kernels each run in one of five launch
  * shapes: 0: 64 threads per block, 1: 128 (default), 2: 256, 3: 128 threads
- * held to 64 registers (eight blocks per SM). Results do not depend on them. */
-#define GKS2L_LAUNCH_SHAPES 4
+ * held to 64 registers (eight blocks per SM), 4: 128 threads held to 128
+ * registers (four blocks per SM). Results do not depend on them. */
+#define GKS2L_LAUNCH_SHAPES 5
 int gks2l_set_launch_shapes(gks2l_ctx *ctx, const int32_t shapes[3]);
 
 /* Autotuner: advances the state by GKS2L_LAUNCH_SHAPES * n_steps full steps,

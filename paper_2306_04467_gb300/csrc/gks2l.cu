@@ -380,6 +380,12 @@ template <typename R>
 __global__ void __launch_bounds__(128, 8) k_edge_r64(Dev d, Par p, int stage) { edge_body<R>(d, p, stage); }
 template <typename R>
 __global__ void __launch_bounds__(128, 8) k_update_r64(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
+template <typename R>
+__global__ void __launch_bounds__(128, 4) k_iface_r128(Dev d) { iface_body<R>(d); }
+template <typename R>
+__global__ void __launch_bounds__(128, 4) k_edge_r128(Dev d, Par p, int stage) { edge_body<R>(d, p, stage); }
+template <typename R>
+__global__ void __launch_bounds__(128, 4) k_update_r128(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
 
 // CFL ratio of the current state (after a state is set)
 __global__ void __launch_bounds__(128) k_cfl(Dev d, Par p) {
@@ -742,14 +748,15 @@ void launch_recon(gks2l_ctx *c, const Par &p) {
 
 // launch shapes the autotuner chooses from: 0: 64 threads, 1: 128 threads,
 // 2: 256 threads (registers as the compiler likes), 3: 128 threads held to
-// 64 registers (eight blocks per SM)
-constexpr int kShapes = 4;
+// 64 registers (eight blocks per SM), 4: 128 threads held to 128 registers
+constexpr int kShapes = 5;
 
 #define GKS2L_SHAPE_SWITCH(cfg, KERNEL, n, st, ...)                                          \
   switch (cfg) {                                                                           \
     case 0: KERNEL<R, 64><<<blocks(n, 64), 64, 0, st>>>(__VA_ARGS__); break;                \
     case 2: KERNEL<R, 256><<<blocks(n, 256), 256, 0, st>>>(__VA_ARGS__); break;             \
     case 3: KERNEL##_r64<R><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;            \
+    case 4: KERNEL##_r128<R><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;           \
     default: KERNEL<R, 128><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;            \
   }
 

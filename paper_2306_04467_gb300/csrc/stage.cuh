@@ -144,12 +144,13 @@ template <typename R>
 __host__ __device__ __forceinline__ void monos(R x, R y, R m[10], R mx[10], R my[10]) {
   const R h = (R)0.5, s = (R)(1.0 / 6.0);
   R xx = x * x, yy = y * y, xy = x * y;
-  m[0] = 1; m[1] = x; m[2] = y; m[3] = h * xx; m[4] = xy; m[5] = h * yy;
+  const R one = (R)1, zero = (R)0;
+  m[0] = one; m[1] = x; m[2] = y; m[3] = h * xx; m[4] = xy; m[5] = h * yy;
   m[6] = xx * x * s; m[7] = h * xx * y; m[8] = h * x * yy; m[9] = yy * y * s;
-  mx[0] = 0; mx[1] = 1; mx[2] = 0; mx[3] = x; mx[4] = y; mx[5] = 0;
-  mx[6] = h * xx; mx[7] = xy; mx[8] = h * yy; mx[9] = 0;
-  my[0] = 0; my[1] = 0; my[2] = 1; my[3] = 0; my[4] = x; my[5] = y;
-  my[6] = 0; my[7] = h * xx; my[8] = xy; my[9] = h * yy;
+  mx[0] = zero; mx[1] = one; mx[2] = zero; mx[3] = x; mx[4] = y; mx[5] = zero;
+  mx[6] = h * xx; mx[7] = xy; mx[8] = h * yy; mx[9] = zero;
+  my[0] = zero; my[1] = zero; my[2] = one; my[3] = zero; my[4] = x; my[5] = y;
+  my[6] = zero; my[7] = h * xx; my[8] = xy; my[9] = h * yy;
 }
 
 template <typename R>
@@ -407,25 +408,23 @@ template <> __device__ __forceinline__ void load_rec<double, 12>(const double *p
 }
 #endif
 
-template <typename R>
-__host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, R x, R y, R href, SideVals<R> &s) {
+// R: the records' precision; T: the values' type (R, or a pair of points)
+template <typename R, typename T = R>
+__host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, T x, T y, T href, SideVals<T> &s) {
   const int N = d.cs;
   R w[NREC], wo[12];
   load_rec<R, NREC>((const R *)d.srec + ((size_t)ell * N + c) * NREC, w);
   load_rec<R, 12>((const R *)d.srec + ((size_t)(1 - ell) * N + c) * NREC, wo);
-  R m[10], mx[10], my[10];
-  monos<R>(x, y, m, mx, my);
+  T m[10], mx[10], my[10];
+  monos<T>(x, y, m, mx, my);
   const R ih = w[11];
-  R dev[3], gx[4], gy[4];
+  T dev[3], gx[4], gy[4];
   for (int i = 0; i < 4; i++) {
     const R *cf = i < 3 ? w + 12 * i : wo;
-    R a = 0, ax = 0, ay = 0;
-    for (int k = 0; k < 10; k++) {
-      R ck = cf[k];
-      a += ck * m[k];
-      ax += ck * mx[k];
-      ay += ck * my[k];
-    }
+    T a = cf[0] * m[0], ax = cf[1] * mx[1], ay = cf[2] * my[2];
+    for (int k = 1; k < 10; k++) a += cf[k] * m[k];
+    for (int k : {3, 4, 6, 7, 8}) ax += cf[k] * mx[k];
+    for (int k : {4, 5, 7, 8, 9}) ay += cf[k] * my[k];
     if (i < 3) dev[i] = a;
     gx[i] = ax * ih;
     gy[i] = ay * ih;
@@ -442,18 +441,18 @@ __host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, 
   if (ell == 0) { gb[0] = w[23]; gb[1] = w[35]; }
   if (xf != 0) {
     const double *M = d.xf + 4 * xf;
-    R mv[2] = {s.mx, s.my};
-    rot2<R>(M, mv);
+    T mv[2] = {s.mx, s.my};
+    rot2<T>(M, mv);
     s.mx = mv[0]; s.my = mv[1];
-    rot2<R>(M, s.glev);
-    rot2<R>(M, s.goth);
+    rot2<T>(M, s.glev);
+    rot2<T>(M, s.goth);
     rot2<R>(M, gb);
-    R T[2][2] = {{s.gm[0][0], s.gm[0][1]}, {s.gm[1][0], s.gm[1][1]}};
+    T G2[2][2] = {{s.gm[0][0], s.gm[0][1]}, {s.gm[1][0], s.gm[1][1]}};
     for (int i2 = 0; i2 < 2; i2++)
       for (int k = 0; k < 2; k++) {
-        R acc = 0;
-        for (int a = 0; a < 2; a++)
-          for (int b2 = 0; b2 < 2; b2++) acc += (R)M[2 * i2 + a] * T[a][b2] * (R)M[2 * k + b2];
+        T acc = (R)M[2 * i2] * G2[0][0] * (R)M[2 * k] + (R)M[2 * i2] * G2[0][1] * (R)M[2 * k + 1];
+        acc += (R)M[2 * i2 + 1] * G2[1][0] * (R)M[2 * k];
+        acc += (R)M[2 * i2 + 1] * G2[1][1] * (R)M[2 * k + 1];
         s.gm[i2][k] = acc;
       }
   }
@@ -623,8 +622,14 @@ __host__ __device__ inline void gks_layer(R href, R dl, R dr, R Ul, R Vl, R Ur, 
     kv[i] = (4 * qh[i] - qd[i]) * id;
     kd[i] = 4 * (qd[i] - 2 * qh[i]) * id * id;
   }
-  R f[3] = {0, 0, 0}, ft[3] = {0, 0, 0}, w[3] = {0, 0, 0}, wt[3] = {0, 0, 0};
-  for (int i = 0; i < 5; i++)
+  R f[3], ft[3], w[3], wt[3];
+  for (int k = 0; k < 3; k++) {
+    w[k] = kv[0] * P[0][k];
+    wt[k] = kd[0] * P[0][k];
+    f[k] = kv[0] * P[0][3 + k];
+    ft[k] = kd[0] * P[0][3 + k];
+  }
+  for (int i = 1; i < 5; i++)
     for (int k = 0; k < 3; k++) {
       w[k] += kv[i] * P[i][k];
       wt[k] += kd[i] * P[i][k];

@@ -222,7 +222,7 @@ class Solver:
         return {"recon": ms[0], "iface": ms[1], "edge": ms[2], "update": ms[3], "step_begin": ms[4], "gate": ms[5]}
 
     def set_launch_shapes(self, shapes):
-        """Launch shapes (0..3) of the interface, edge and update kernels."""
+        """Launch shapes (0..4) of the interface, edge and update kernels."""
         b = (ctypes.c_int32 * 3)(*[int(x) for x in shapes])
         _check(load().gks2l_set_launch_shapes(self._h, ctypes.byref(b)), "gks2l_set_launch_shapes")
 

@@ -37,7 +37,7 @@ def test_launch_shapes_leave_results_unchanged(precision):
     ref = g.problem_solver(prob, precision=precision)
     ref.advance(20)
     a0, g0 = ref.get_state()
-    for shapes in ([0, 0, 0], [2, 2, 2], [3, 3, 3], [0, 3, 2]):
+    for shapes in ([0, 0, 0], [2, 2, 2], [3, 3, 3], [4, 4, 4], [0, 3, 2]):
         s = g.problem_solver(prob, precision=precision)
         s.set_launch_shapes(shapes)
         s.advance(20)
@@ -50,15 +50,15 @@ def test_autotune_advances_like_advance():
     prob.avg[3] += 0.01 * np.sin(np.arange(prob.mesh.n_tri))
     s = g.problem_solver(prob, precision=g.GKS2L_FP32)
     shapes = s.autotune(1)
-    assert len(shapes) == 3 and all(0 <= b < 4 for b in shapes)
+    assert len(shapes) == 3 and all(0 <= b < 5 for b in shapes)
     s.advance(6)
     a, gr = s.get_state()
     ref = g.problem_solver(prob, precision=g.GKS2L_FP32)
-    ref.advance(4 * 2 + 6)
+    ref.advance(5 * 2 + 6)
     b, h = ref.get_state()
     assert np.array_equal(a, b) and np.array_equal(gr, h)
     with pytest.raises(g.GKSError):
-        s.set_launch_shapes([0, 4, 0])
+        s.set_launch_shapes([0, 5, 0])
 
 
 @pytest.mark.parametrize("precision", [g.GKS2L_FP64, g.GKS2L_FP32])
