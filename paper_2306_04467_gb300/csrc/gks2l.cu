@@ -281,22 +281,22 @@ __device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage)
   } else {
     for (int k = 0; k < 12; k++) out[k] = 0;
   }
+  // the Gauss point q = 0 thread averages the fluxes (out[0..5]), the q = 1
+  // thread the interface values (out[6..11]): each sends the other its half
+  R avg[6];
 #pragma unroll
-  for (int k = 0; k < 12; k++) out[k] = (R)0.5 * (out[k] + __shfl_xor_sync(FULL, out[k], 1));
+  for (int k = 0; k < 6; k++) {
+    const R mine = q == 0 ? out[k] : out[6 + k], theirs = q == 0 ? out[6 + k] : out[k];
+    avg[k] = (R)0.5 * (mine + __shfl_xor_sync(FULL, theirs, 1));
+  }
   if (!ok) return;
   const int NE = d.ne;
   const int vb = ell == 0 ? 3 : 0;
-  if (q == 0) {
-    for (int k = 0; k < 3; k++) {
-      ((R *)d.eF)[(vb + k) * NE + e] = out[k];
-      ((R *)d.eFt)[(vb + k) * NE + e] = out[3 + k];
-    }
-  } else {
-    R *Wd = (R *)(stage == 1 ? d.eWn : d.eW);
-    for (int k = 0; k < 3; k++) {
-      Wd[(vb + k) * NE + e] = out[6 + k];
-      ((R *)d.eWt)[(vb + k) * NE + e] = out[9 + k];
-    }
+  R *A = (R *)(q == 0 ? d.eF : (stage == 1 ? d.eWn : d.eW));
+  R *B = (R *)(q == 0 ? d.eFt : d.eWt);
+  for (int k = 0; k < 3; k++) {
+    A[(vb + k) * NE + e] = avg[k];
+    B[(vb + k) * NE + e] = avg[3 + k];
   }
 }
 

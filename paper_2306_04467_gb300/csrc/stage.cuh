@@ -491,6 +491,29 @@ __host__ __device__ __forceinline__ void half_moments(R U, R lam, R sgn, R mu[6]
   mu[5] = 4 * th * mu[3] + pw;
 }
 
+// both half lines of one Maxwellian (sgn = +1 into mp, -1 into mm), sharing
+// its error function and exponential
+template <typename R>
+__host__ __device__ __forceinline__ void half_moments_pm(R U, R lam, R mp[6], R mm[6]) {
+  const R th = (R)0.5 / lam;
+  const R e0 = (R)0.5 * r_erf<R>(r_sqrt<R>(lam) * U);
+  const R E = r_exp<R>(-lam * U * U) * (R)0.5 / r_sqrt<R>((R)3.14159265358979323846 * lam);
+  for (int sg = 0; sg < 2; sg++) {
+    const R sgn = sg == 0 ? (R)1 : (R)-1;
+    R *mu = sg == 0 ? mp : mm;
+    mu[0] = (R)0.5 + sgn * e0;
+    mu[1] = sgn * E;
+    R pw = -sgn * U * E;
+    mu[2] = th * mu[0] + pw;
+    pw *= -U;
+    mu[3] = 2 * th * mu[1] + pw;
+    pw *= -U;
+    mu[4] = 3 * th * mu[2] + pw;
+    pw *= -U;
+    mu[5] = 4 * th * mu[3] + pw;
+  }
+}
+
 // Slope + force kernel on a Maxwellian base (h, U, V, lam), written as a
 // polynomial in c = u - U: the exact derivative of ln g along n and t, plus
 // the force term, whose cubic part combines into (lam/h) |c|^2 (D . c) with
@@ -531,17 +554,24 @@ __host__ __device__ __forceinline__ void kern_moments(const Kern<R> &K, const R 
   out[5] = U * V * T00 + V * T10 + U * T01 + T11;
 }
 
-// time integrals over [0, delta] of C1..C5
+// time integrals over [0, delta] of C1..C5, from e = exp(-delta/tau) and
+// em = 1 - e
 template <typename R>
-__host__ __device__ __forceinline__ void time_ints(R tau, R delta, R q[5]) {
-  R x = delta / tau;
-  R em = -r_expm1<R>(-x);
-  R e = r_exp<R>(-x);
+__host__ __device__ __forceinline__ void time_ints_e(R tau, R delta, R e, R em, R q[5]) {
   q[0] = delta - tau * em;
   q[1] = -tau * delta * (1 + e) + 2 * tau * tau * em;
   q[2] = (R)0.5 * delta * delta - tau * delta + tau * tau * em;
   q[3] = tau * em;
   q[4] = tau * delta * e - tau * tau * em;
+}
+// the same over [0, delta] (qd) and [0, delta / 2] (qh); the full interval's
+// exponentials follow from the half interval's: e = eh^2, 1 - e = emh (1 + eh)
+template <typename R>
+__host__ __device__ __forceinline__ void time_ints2(R tau, R delta, R qd[5], R qh[5]) {
+  const R xh = (R)0.5 * delta / tau;
+  const R emh = -r_expm1<R>(-xh), eh = r_exp<R>(-xh);
+  time_ints_e<R>(tau, (R)0.5 * delta, eh, emh, qh);
+  time_ints_e<R>(tau, delta, eh * eh, emh * (1 + eh), qd);
 }
 
 // One layer at one Gauss point, local frame (x along the normal from L to R).
@@ -576,9 +606,8 @@ __host__ __device__ inline void gks_layer(R href, R dl, R dr, R Ul, R Vl, R Ur, 
   const R hbR = hb + hdev;
   const R Ub = mbn / hbR, Vb = mbt / hbR;
   const R lamb = 1 / (g * hbR), thb = (R)0.5 * g * hbR;
-  R mbp[6], mbm[6], t0, t1;
-  half_moments<R>(Ub, lamb, (R)1, mbp, t0, t1);
-  half_moments<R>(Ub, lamb, (R)-1, mbm, t0, t1);
+  R mbp[6], mbm[6];
+  half_moments_pm<R>(Ub, lamb, mbp, mbm);
   Kern<R> kbl = make_kern<R>(hbR, Ub, Vb, lamb, dnl, dtl, Dl);
   Kern<R> kbr = make_kern<R>(hbR, Ub, Vb, lamb, dnr, dtr, Dr);
   Kern<R> kl = make_kern<R>(hlR, Ul, Vl, laml, dnl, dtl, Dl);
@@ -614,8 +643,7 @@ __host__ __device__ inline void gks_layer(R href, R dl, R dr, R Ul, R Vl, R Ur, 
   P[3][5] = hlR * Vl * (Ul * mul[0] + mul[1]) + hrR * Vr * (Ur * mur[0] + mur[1]);
   // fitted value and derivative at the stage start
   R qd[5], qh[5];
-  time_ints<R>(tau, delta, qd);
-  time_ints<R>(tau, (R)0.5 * delta, qh);
+  time_ints2<R>(tau, delta, qd, qh);
   R kv[5], kd[5];
   const R id = 1 / delta;
   for (int i = 0; i < 5; i++) {
