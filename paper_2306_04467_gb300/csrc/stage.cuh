@@ -460,6 +460,34 @@ __host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, 
   s.gh[1] = s.glev[1] - gb[1];
 }
 
+// the values only (level deviation, depth, discharge) of cell c's layer-ell
+// reconstruction at scaled point (x, y) through transform xf
+template <typename R>
+__host__ __device__ inline void side_values(const Dev &d, int ell, int c, int xf, R x, R y, R href, R &dv, R &h,
+                                            R &mx, R &my) {
+  R w[NREC];
+  load_rec<R, NREC>((const R *)d.srec + ((size_t)ell * d.cs + c) * NREC, w);
+  const R hh = (R)0.5, s6 = (R)(1.0 / 6.0);
+  const R xx = x * x, yy = y * y, xy = x * y;
+  const R m[10] = {(R)1, x, y, hh * xx, xy, hh * yy, xx * x * s6, hh * xx * y, hh * x * yy, yy * y * s6};
+  R v[3];
+  for (int i = 0; i < 3; i++) {
+    R a = w[12 * i] * m[0];
+    for (int k = 1; k < 10; k++) a += w[12 * i + k] * m[k];
+    v[i] = w[12 * i + 10] + a;
+  }
+  dv = v[0];
+  h = href + v[0];
+  mx = v[1];
+  my = v[2];
+  if (xf != 0) {
+    R mv[2] = {mx, my};
+    rot2<R>(d.xf + 4 * xf, mv);
+    mx = mv[0];
+    my = mv[1];
+  }
+}
+
 // depth of the reference level at Gauss point q of edge e for layer ell
 template <typename R>
 __host__ __device__ __forceinline__ R ref_depth(const Dev &d, int ell, int e, int q) {
@@ -684,14 +712,14 @@ __host__ __device__ inline R iface_unit(const Dev &d, int e, int ell, int q) {
   const R *xl = (const R *)d.exiL, *xr = (const R *)d.exiR, *en = (const R *)d.en;
   int cL = d.eL[e], cR = d.eR[e], xf = d.exf[e];
   const R href = ref_depth<R>(d, ell, e, q);
-  SideVals<R> sl, sr;
-  side_vals<R>(d, ell, cL, 0, xl[(2 * q) * NE + e], xl[(2 * q + 1) * NE + e], href, sl);
-  side_vals<R>(d, ell, cR, xf, xr[(2 * q) * NE + e], xr[(2 * q + 1) * NE + e], href, sr);
+  R dl, hl, mxl, myl, dr, hr, mxr, myr;
+  side_values<R>(d, ell, cL, 0, xl[(2 * q) * NE + e], xl[(2 * q + 1) * NE + e], href, dl, hl, mxl, myl);
+  side_values<R>(d, ell, cR, xf, xr[(2 * q) * NE + e], xr[(2 * q + 1) * NE + e], href, dr, hr, mxr, myr);
   const R n0 = en[e], n1 = en[NE + e];
-  R ul = (sl.mx * n0 + sl.my * n1) / sl.h;
-  R ur = (sr.mx * n0 + sr.my * n1) / sr.h;
+  R ul = (mxl * n0 + myl * n1) / hl;
+  R ur = (mxr * n0 + myr * n1) / hr;
   R xi = (R)0.5 * r_erfc<R>((R)0.5 * (ul + ur));
-  return sr.d + xi * (sl.d - sr.d);
+  return dr + xi * (dl - dr);
 }
 
 // plane gradient (Sec. 2.3) of the blended level `which` for cell c
