@@ -31,7 +31,7 @@ MEAN = g.GKS2L_MLP_NTRAIN
 ISTD = MEAN + N_IN
 
 
-def collect(problems, precision=g.GKS2L_FP32, snapshots=8, stride=20, tol=1e-2):
+def collect(problems, precision=g.GKS2L_FP32, snapshots=8, stride=20, tol=3e-3):
     """Harvest (features, labels) from runs of each problem: every cell every
     `stride` stages. The reconstruction decides with the gate its previous
     stage computed, so a cell's label marks it troubled at this stage or the
@@ -125,7 +125,7 @@ def evaluate(X, y, P, threshold=THRESHOLD):
                 label_fraction=float(pos.float().mean().item()))
 
 
-def default_gate(precision=g.GKS2L_FP32, tol=1e-2, steps=1500, seed=2312, scale=1):
+def default_gate(precision=g.GKS2L_FP32, tol=3e-3, steps=1500, seed=2312, scale=1):
     """Harvest from `training_problems(scale)` and train: the gate the
     benchmark and tests use. Returns (params, quality on the training set)."""
     X, y = collect(training_problems(scale), precision=precision, tol=tol)
