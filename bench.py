@@ -55,8 +55,8 @@ N_SQ = 1024
 # update: three edges' fluxes and interface values, state in/out with the
 # S2O4 snapshot, mirrors out). Units: cells for recon, gate and update, edges for iface and edge.
 WORK_PER_UNIT = {
-    "fp32": {"recon": (2195, 0, 1069), "gate": (280, 0, 51), "iface": (930, 0, 265), "edge": (6981, 0, 374),
-             "update": (331, 73, 570)},
+    "fp32": {"recon": (2196, 0, 1069), "gate": (280, 0, 51), "iface": (906, 0, 265), "edge": (6239, 0, 374),
+             "update": (332, 61, 570)},
     "fp64": {"recon": (69, 4593, 2209), "gate": (280, 0, 63), "iface": (15, 1349, 473), "edge": (107, 9162, 696),
              "update": (0, 343, 850)},
 }
@@ -64,7 +64,7 @@ WORK_PER_UNIT = {
 PEAK_TFLOPS = {"fp32": 76.5, "fp64": 1.254}
 # DRAM bytes per unit (dram__bytes_read.sum + dram__bytes_write.sum of the
 # same launches, per unit; inputs larger than L2, traffic grows with units).
-TRAFFIC_PER_UNIT = {"fp32": {"recon": 971.0, "gate": 51.0, "iface": 245.0, "edge": 357.0, "update": 461.0}}
+TRAFFIC_PER_UNIT = {"fp32": {"recon": 1023.0, "gate": 51.0, "iface": 260.0, "edge": 362.0, "update": 456.0}}
 
 
 def roofline(form, kernel, units, ms, hbm_gbs):
