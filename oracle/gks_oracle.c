@@ -328,7 +328,7 @@ static int build_mesh(orc_t *o) {
       he[3 * c + k].k = k;
     }
   qsort(he, 3 * nt, sizeof(hedge_t), hedge_cmp);
-  o->edge = calloc(3 * nt, sizeof(edge_t));
+  o->edge = calloc((size_t)3 * (size_t)nt, sizeof(edge_t));
   int ne = 0;
   int *bnd = malloc(sizeof(int) * 3 * nt), nb = 0;   /* boundary half-edges */
   for (int i = 0; i < 3 * nt;) {
