@@ -11,8 +11,6 @@
 //                                    gradients (Eqs. SWE-semi-flux, slope-1, S2O3),
 //                                    CFL and conservation reductions
 // A step is k_step_begin + two stages, captured once into a CUDA graph.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,32 +36,38 @@ constexpr int ST_TIMEOUT = 4;           // status bit: a bounded wait gave up
 constexpr int GATE_LD = 40;             // padded row stride of the gate feature tile (bank spread)
 
 // ---------------------------------------------------------------- TMA staging
-// Operator rows of one tile of TW cells in shared memory, [row][TW] each.
-struct ReconMaps {
-  CUtensorMap lsq, p1, bq, mm, st, sx;
-};
-
+// The reconstruction's operator rows of one tile of TW cells, [row][TW] per
+// group, stored contiguously per tile in global memory and copied as they lie
+// into shared memory by the bulk-copy engine. The groups come in the order
+// the copies need them: what every tile uses (P3 least-squares rows, monomial
+// means, stencil cells and their transforms), then what only tiles with a
+// troubled cell use (P1 candidate rows, smoothness forms), so a tile the gate
+// calls smooth fetches one prefix.
 template <typename R> struct TileLayout {
   static constexpr unsigned LSQ = 0;
-  static constexpr unsigned P1 = LSQ + kCoef * kCols * TW * sizeof(R);
-  static constexpr unsigned BQ = P1 + 30 * TW * sizeof(R);
-  static constexpr unsigned MM = BQ + kBeta * TW * sizeof(R);
+  static constexpr unsigned MM = LSQ + kCoef * kCols * TW * sizeof(R);
   static constexpr unsigned ST = MM + 7 * TW * sizeof(R);
   static constexpr unsigned SX = ST + kSlots * TW * 4;
-  static constexpr unsigned BAR = SX + 384;                   // 9 * 32 int8 rounded to 128 B
-  static constexpr unsigned BYTES = BAR + 16;
-  static_assert(2 * TW * NREC * sizeof(R) <= P1 - LSQ, "side-record staging fits in the LSQ rows");
-  static constexpr unsigned TX = BAR - 96;                    // bytes the six copies deliver
-  static constexpr unsigned TX_LINEAR = TX - (MM - P1);       // without the P1 and beta rows
+  static constexpr unsigned P1 = SX + kSlots * TW;
+  static constexpr unsigned BQ = P1 + 30 * TW * sizeof(R);
+  static constexpr unsigned END = BQ + kBeta * TW * sizeof(R);
+  static constexpr unsigned TILE = (END + 127) / 128 * 128;   // tile stride in global memory
+  static constexpr unsigned BAR = (END + 127) / 128 * 128;    // buffer stride in shared memory
+  static constexpr unsigned TX_LINEAR = P1;                    // bytes of the first copy
+  static constexpr unsigned TX = END;                          // bytes of both copies
+  static_assert(2 * TW * NREC * sizeof(R) <= MM - LSQ, "side-record staging fits in the LSQ rows");
+  static_assert(P1 % 16 == 0 && END % 16 == 0, "bulk copies move multiples of 16 bytes");
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, void *bar) {
+// bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to shared memory, completing on the mbarrier
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, void *bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
           smem_addr(dst)),
-      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_addr(bar))
+      "l"((unsigned long long)__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
 
@@ -83,23 +87,27 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// wait for phase 0 of an mbarrier for at most ~limit_ns
-__device__ __forceinline__ bool mbar_wait_bounded(void *bar, unsigned long long limit_ns) {
+// wait for the phase of the given parity of an mbarrier for at most ~limit_ns
+__device__ __forceinline__ bool mbar_wait_bounded(void *bar, unsigned parity, unsigned long long limit_ns) {
   unsigned long long t0 = global_ns();
   for (int it = 0; it < (1 << 24); it++) {
-    if (mbar_try_wait(bar, 0)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
     if (global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
 
 // ------------------------------------------------------------------ kernels
-// resident reconstruction blocks per SM the register budget is held to
+// resident reconstruction blocks per SM the register budget is held to (a
+// block per tile keeps 36 warps per SM on the neighbour gathers; persistent
+// blocks with two operator buffers, fetching the next tile during the
+// current one, halve that and run slower)
 template <typename R> struct ReconOcc { static constexpr int value = 6; };
 template <> struct ReconOcc<double> { static constexpr int value = 4; };
+template <typename R> constexpr unsigned recon_smem() { return TileLayout<R>::BAR + 16; }
 
 template <typename R>
-__global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p, const __grid_constant__ ReconMaps maps) {
+__global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p) {
   using T = TileLayout<R>;
   extern __shared__ __align__(128) unsigned char sm[];
   const int j0 = blockIdx.x * TW;
@@ -111,27 +119,22 @@ __global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p,
   const unsigned lin_mask = gate_on ? d.gate_mask[blockIdx.x] : 0u;
   const bool all_linear = lin_mask == 0xffffffffu;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const unsigned char *src = (const unsigned char *)d.ops + (size_t)blockIdx.x * T::TILE;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
                  "r"(all_linear ? T::TX_LINEAR : T::TX)
                  : "memory");
-    tma_load_2d(sm + T::LSQ, &maps.lsq, j0, 0, bar);
-    if (!all_linear) {
-      tma_load_2d(sm + T::P1, &maps.p1, j0, 0, bar);
-      tma_load_2d(sm + T::BQ, &maps.bq, j0, 0, bar);
-    }
-    tma_load_2d(sm + T::MM, &maps.mm, j0, 0, bar);
-    tma_load_2d(sm + T::ST, &maps.st, j0, 0, bar);
-    tma_load_2d(sm + T::SX, &maps.sx, j0, 0, bar);
+    bulk_load(sm, src, T::TX_LINEAR, bar);
+    if (!all_linear) bulk_load(sm + T::P1, src + T::P1, T::TX - T::TX_LINEAR, bar);
   }
   __syncthreads();
-  const bool landed = mbar_wait_bounded(bar, 1000000000ull);
+  const bool landed = mbar_wait_bounded(bar, 0, 1000000000ull);
   if (!__syncthreads_and(landed)) {
     // the copies did not land within a second: report, wait for them once
     // more (bounded) so no copy outlives the block, and leave (all threads)
     if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(d.status, ST_TIMEOUT);
-    if (!landed) mbar_wait_bounded(bar, 1000000000ull);
+    if (!landed) mbar_wait_bounded(bar, 0, 1000000000ull);
     return;
   }
   const int j = j0 + threadIdx.x, v = threadIdx.y;
@@ -539,7 +542,6 @@ struct gks2l_ctx {
   size_t ws_bytes = 0;
   cudaStream_t stream = nullptr;
   Dev d{};
-  ReconMaps maps{};
   int *d_perm = nullptr;
   double *d_tend = nullptr;
   double *d_stage = nullptr;   // 18 * nt staging for permutations
@@ -579,10 +581,7 @@ size_t layout(gks2l_ctx *c, char *base) {
   d.bgy = k.take<double>(nt);
   d.st_cell = k.take<int>(kSlots * cs);
   d.st_xf = k.take<int8_t>(kSlots * cs);
-  d.lsq = k.take<char>(rs * kCoef * kCols * cs);
-  d.p1op = k.take<char>(rs * 30 * cs);
-  d.bq = k.take<char>(rs * kBeta * cs);
-  d.mmean = k.take<char>(rs * 7 * cs);
+  d.ops = k.take<char>((cs / TW) * (rs == 4 ? TileLayout<float>::TILE : TileLayout<double>::TILE));
   d.plane = k.take<char>(rs * 6 * cs);
   d.cedge = k.take<int>(3 * cs);
   d.fsl = k.take<double>(3 * cs);
@@ -662,6 +661,43 @@ int upload_form(gks2l_ctx *c, const void *dst, const std::vector<double> &src, i
   return upload(c, dst, src);
 }
 
+// the reconstruction's operator rows, tile by tile in the layout k_recon
+// copies (TileLayout), in the form's precision; packed on the host a batch of
+// tiles at a time (cells past the end are zero)
+template <typename R>
+int upload_tiles(gks2l_ctx *c) {
+  using T = TileLayout<R>;
+  const Prep &P = c->prep;
+  const size_t nt = P.nt, ntile = c->cs / TW, batch = 1024;
+  std::vector<unsigned char> buf(batch * T::TILE);
+  for (size_t t0 = 0; t0 < ntile; t0 += batch) {
+    const size_t nb = std::min(batch, ntile - t0);
+    std::fill(buf.begin(), buf.end(), (unsigned char)0);
+    for (size_t t = 0; t < nb; t++) {
+      unsigned char *b = buf.data() + t * T::TILE;
+      R *lsq = (R *)(b + T::LSQ), *mm = (R *)(b + T::MM), *p1 = (R *)(b + T::P1), *bq = (R *)(b + T::BQ);
+      int *st = (int *)(b + T::ST);
+      int8_t *sx = (int8_t *)(b + T::SX);
+      for (int i = 0; i < TW; i++) {
+        const size_t j = (t0 + t) * TW + i;
+        if (j >= nt) break;
+        for (int r = 0; r < kCoef * kCols; r++) lsq[r * TW + i] = (R)P.lsq[r * nt + j];
+        for (int r = 0; r < 7; r++) mm[r * TW + i] = (R)P.mmean[r * nt + j];
+        for (int r = 0; r < kSlots; r++) {
+          st[r * TW + i] = P.st_cell[r * nt + j];
+          sx[r * TW + i] = P.st_xf[r * nt + j];
+        }
+        for (int r = 0; r < 30; r++) p1[r * TW + i] = (R)P.p1op[r * nt + j];
+        for (int r = 0; r < kBeta; r++) bq[r * TW + i] = (R)P.bq[r * nt + j];
+      }
+    }
+    CK(cudaMemcpyAsync((char *)c->d.ops + t0 * T::TILE, buf.data(), nb * T::TILE, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return 0;
+}
+
 inline unsigned blocks(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
 int upload_bathymetry(gks2l_ctx *c) {
@@ -694,46 +730,6 @@ Par make_par(const gks2l_ctx *c) {
 }
 
 
-// tensor maps of the per-cell operator rows ([rows][cs], tiles of TW cells)
-int make_maps(gks2l_ctx *c) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
-      c->err = "cuTensorMapEncodeTiled not available";
-      return GKS2L_ECUDA;
-    }
-    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-  }
-  const bool f32 = c->rsize == 4;
-  auto one = [&](CUtensorMap *m, const void *base, CUtensorMapDataType t, size_t esize, unsigned rows) -> int {
-    cuuint64_t dims[2] = {(cuuint64_t)c->cs, rows};
-    cuuint64_t strides[1] = {(cuuint64_t)c->cs * esize};
-    cuuint32_t box[2] = {(cuuint32_t)TW, rows};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = encode(m, t, 2, (void *)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-      c->err = "cuTensorMapEncodeTiled failed";
-      return GKS2L_ECUDA;
-    }
-    return 0;
-  };
-  const CUtensorMapDataType rt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-  const size_t rs = c->rsize;
-  int rc;
-  if ((rc = one(&c->maps.lsq, c->d.lsq, rt, rs, kCoef * kCols)) || (rc = one(&c->maps.p1, c->d.p1op, rt, rs, 30)) ||
-      (rc = one(&c->maps.bq, c->d.bq, rt, rs, kBeta)) || (rc = one(&c->maps.mm, c->d.mmean, rt, rs, 7)) ||
-      (rc = one(&c->maps.st, c->d.st_cell, CU_TENSOR_MAP_DATA_TYPE_INT32, 4, kSlots)) ||
-      (rc = one(&c->maps.sx, c->d.st_xf, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, kSlots)))
-    return rc;
-  return 0;
-}
-
 template <typename R>
 void launch_gate(gks2l_ctx *c, const Par &p, cudaStream_t st) {
   const unsigned nb = std::min(blocks(c->d.nt, 4 * TW), (unsigned)(c->n_sm * GATE_BLOCKS_PER_SM));
@@ -743,7 +739,7 @@ void launch_gate(gks2l_ctx *c, const Par &p, cudaStream_t st) {
 template <typename R>
 void launch_recon(gks2l_ctx *c, const Par &p) {
   const Dev &d = c->d;
-  k_recon<R><<<blocks(d.nt, TW), dim3(TW, 6), TileLayout<R>::BYTES, c->stream>>>(d, p, c->maps);
+  k_recon<R><<<blocks(d.nt, TW), dim3(TW, 6), recon_smem<R>(), c->stream>>>(d, p);
 }
 
 // launch shapes the autotuner chooses from: 0: 64 threads, 1: 128 threads,
@@ -994,21 +990,20 @@ int gks2l_bind(gks2l_ctx *c, void *d_workspace, size_t bytes, void *stream) {
       (rc = upload_rows<int>(c, c->d.cedge, P.cedge, 3)) || (rc = upload_rows<double>(c, c->d.fsl, fsl, 3)) ||
       (rc = upload(c, c->d.inst_first, P.inst_first)) || (rc = upload(c, c->d.eL, P.eL)) ||
       (rc = upload(c, c->d.eR, P.eR)) || (rc = upload(c, c->d.exf, P.exf)) || (rc = upload(c, c->d.xf, xf)) ||
-      (rc = upload(c, c->d_perm, P.perm)) || (rc = upload_form(c, c->d.lsq, P.lsq, kCoef * kCols, true)) ||
-      (rc = upload_form(c, c->d.p1op, P.p1op, 30, true)) || (rc = upload_form(c, c->d.bq, P.bq, kBeta, true)) ||
-      (rc = upload_form(c, c->d.mmean, P.mmean, 7, true)) || (rc = upload_form(c, c->d.plane, P.plane, 6, true)) ||
+      (rc = upload(c, c->d_perm, P.perm)) ||
+      (rc = c->rsize == 4 ? upload_tiles<float>(c) : upload_tiles<double>(c)) ||
+      (rc = upload_form(c, c->d.plane, P.plane, 6, true)) ||
       (rc = upload_form(c, c->d.hsR, P.hs, 1, false)) || (rc = upload_form(c, c->d.ihsR, ihs, 1, false)) ||
       (rc = upload_form(c, c->d.epsA, epsA, 1, false)) || (rc = upload_form(c, c->d.exiL, P.exiL, 1, false)) ||
       (rc = upload_form(c, c->d.exiR, P.exiR, 1, false)) || (rc = upload_form(c, c->d.en, en, 1, false)))
     return rc;
-  if ((rc = make_maps(c))) return rc;
   {
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev));
   }
-  CK(cudaFuncSetAttribute(k_recon<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileLayout<float>::BYTES));
-  CK(cudaFuncSetAttribute(k_recon<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileLayout<double>::BYTES));
+  CK(cudaFuncSetAttribute(k_recon<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, recon_smem<float>()));
+  CK(cudaFuncSetAttribute(k_recon<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, recon_smem<double>()));
   c->bound = true;
   c->has_state = false;
   return upload_bathymetry(c);

@@ -60,7 +60,7 @@ struct Dev {
   const double *bmean, *bgx, *bgy;
   const int *st_cell;
   const int8_t *st_xf;
-  const void *lsq, *p1op, *bq, *mmean;
+  const void *ops;          // per tile of 32 cells: the reconstruction's operator rows
   const void *plane;        // [(f*2+d)][cell] plane operator, type R
   const int *cedge;         // [f][cell]: edge id, or ~edge when the cell is the R side
   const double *fsl;        // [f][cell]: sign * |Gamma| / |Omega| (double, mass sums)
@@ -202,23 +202,14 @@ __host__ __device__ __forceinline__ void img_dg(const Dev &d, int v, int c, int 
 }
 
 // --------------------------------------------------- compact reconstruction
-// Per-cell operator rows of one cell: element k of row r is at
-// base[r * stride + idx] (global arrays: stride = cell stride, idx = cell;
-// a staged shared-memory tile: stride = tile width, idx = cell in the tile).
+// Operator rows of one cell: element k of row r is at base[r * stride + idx]
+// (a tile staged in shared memory: stride = tile width, idx = cell in the tile).
 template <typename R> struct CellOps {
   const R *lsq, *p1, *bq, *mm;
   const int *st;
   const int8_t *sx;
   int stride, idx;
 };
-
-template <typename R>
-__host__ __device__ __forceinline__ CellOps<R> global_ops(const Dev &d, int j) {
-  CellOps<R> o;
-  o.lsq = (const R *)d.lsq; o.p1 = (const R *)d.p1op; o.bq = (const R *)d.bq; o.mm = (const R *)d.mmean;
-  o.st = d.st_cell; o.sx = d.st_xf; o.stride = d.cs; o.idx = j;
-  return o;
-}
 
 // One cell and one variable: P3 least squares (Eq. Recons-system), three P1
 // candidates on {cell, face neighbour}, smoothness indicators and WENO-Z
@@ -335,23 +326,6 @@ __host__ __device__ inline void recon_finish(const Dev &d, const Par &p, const C
   p0[10] = q0;
   if (v == 3) ((R *)d.omg)[j] = fac;
   if (v == 0) ((R *)d.omg)[N + j] = fac;
-}
-
-template <typename R>
-__host__ __device__ inline void recon_unit(const Dev &d, const Par &p, const CellOps<R> &o, int j, int v,
-                                           bool linear) {
-  R rhs[NCOL], a[9];
-  recon_gather<R>(d, o, j, v, rhs);
-  recon_p3<R>(o, rhs, a);
-  recon_finish<R>(d, p, o, j, v, rhs, a, linear);
-  if (v == 5) {
-    // the side records' constant words: 1/h_s and the bottom slope
-    R *r0 = (R *)d.srec + (size_t)j * NREC, *r1 = (R *)d.srec + ((size_t)d.cs + j) * NREC;
-    r0[11] = r1[11] = ((const R *)d.ihsR)[j];
-    r0[23] = ((const R *)d.bgR)[j];
-    r0[35] = ((const R *)d.bgR)[d.cs + j];
-    r1[23] = r1[35] = 0;
-  }
 }
 
 // ------------------------------------------------- evaluation at an edge point
