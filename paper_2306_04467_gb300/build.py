@@ -41,6 +41,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
                    "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
             if s.endswith(".cu"):
                 cmd[1:1] = ["-Xptxas", "-v"] if verbose else []
+            if s == "gks2l.cu":
+                # the stage kernels' single-precision divisions and square
+                # roots as the hardware's approximate forms (FP64 untouched)
+                cmd[1:1] = ["-prec-div=false", "-prec-sqrt=false"]
             jobs.append(cmd)
     with ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))

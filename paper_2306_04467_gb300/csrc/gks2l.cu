@@ -98,11 +98,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(void *bar, unsigned parity, un
 }
 
 // ------------------------------------------------------------------ kernels
-// resident reconstruction blocks per SM the register budget is held to (a
-// block per tile keeps 36 warps per SM on the neighbour gathers; persistent
-// blocks with two operator buffers, fetching the next tile during the
-// current one, halve that and run slower)
-template <typename R> struct ReconOcc { static constexpr int value = 6; };
+// resident reconstruction blocks per SM the register budget is held to (in
+// FP32 seven, as many as the shared memory holds: a block per tile keeps 42
+// warps per SM on the neighbour gathers; persistent blocks with two operator
+// buffers, fetching the next tile during the current one, halve the warps
+// and run slower)
+template <typename R> struct ReconOcc { static constexpr int value = 7; };
 template <> struct ReconOcc<double> { static constexpr int value = 4; };
 template <typename R> constexpr unsigned recon_smem() { return TileLayout<R>::BAR + 16; }
 

@@ -118,7 +118,15 @@ template <> __host__ __device__ __forceinline__ double r_erfc<double>(double x) 
 template <> __host__ __device__ __forceinline__ float r_erfc<float>(float x) { return erfcf(x); }
 template <typename R> __host__ __device__ __forceinline__ R r_exp(R x);
 template <> __host__ __device__ __forceinline__ double r_exp<double>(double x) { return exp(x); }
-template <> __host__ __device__ __forceinline__ float r_exp<float>(float x) { return expf(x); }
+// single precision on the device: the hardware exponential (a few ulp; the
+// arguments here are O(1) Maxwellian exponents and -delta/tau)
+template <> __host__ __device__ __forceinline__ float r_exp<float>(float x) {
+#ifdef __CUDA_ARCH__
+  return __expf(x);
+#else
+  return expf(x);
+#endif
+}
 template <typename R> __host__ __device__ __forceinline__ R r_expm1(R x);
 template <> __host__ __device__ __forceinline__ double r_expm1<double>(double x) { return expm1(x); }
 template <> __host__ __device__ __forceinline__ float r_expm1<float>(float x) { return expm1f(x); }
