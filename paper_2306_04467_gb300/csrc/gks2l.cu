@@ -5,7 +5,7 @@
 //   k_recon   (32 cells x 6 variables per block) compact P3/WENO reconstruction
 //             (Sec. 3.4); the block's operator rows are staged into shared
 //             memory by TMA (cp.async.bulk.tensor) behind an mbarrier
-//   k_iface   (edge x layer x point) blended interface levels h-hat (Sec. 2.3)
+//   k_iface   (edge x layer)         blended interface levels h-hat (Sec. 2.3)
 //   k_edge    (edge x layer x point) gas-kinetic interface solution (Eq. SWE-2nd-order)
 //   k_update  (cell)                 fluxes, sources, S2O4 update, Gauss-theorem
 //                                    gradients (Eqs. SWE-semi-flux, slope-1, S2O3),
@@ -263,13 +263,9 @@ __global__ void k_harvest(Dev d, const int *perm, float tol, const float *logit_
 template <typename R>
 __device__ __forceinline__ void iface_body(const Dev &d) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  int e = tid >> 2, ell = (tid >> 1) & 1, q = tid & 1;
-  bool ok = e < d.ne;
-  int ee = ok ? e : d.ne - 1;
-  ok = ok && d.dt[d.inst[d.eL[ee]]] > 0;
-  R v = ok ? iface_unit<R>(d, ee, ell, q) : (R)0;
-  R s = v + __shfl_xor_sync(FULL, v, 1);
-  if (ok && q == 0) ((R *)d.hc)[ell * d.ne + e] = (R)0.5 * s;
+  int e = tid >> 1, ell = tid & 1;
+  if (e >= d.ne || !(d.dt[d.inst[d.eL[e]]] > 0)) return;
+  ((R *)d.hc)[ell * d.ne + e] = iface_unit<R>(d, e, ell);
 }
 
 template <typename R>
@@ -759,7 +755,7 @@ constexpr int kShapes = 5;
 
 template <typename R>
 void launch_iface(gks2l_ctx *c, cudaStream_t st) {
-  const size_t n = 4 * (size_t)c->d.ne;
+  const size_t n = 2 * (size_t)c->d.ne;
   GKS2L_SHAPE_SWITCH(c->shape[0], k_iface, n, st, c->d)
 }
 

@@ -442,31 +442,17 @@ __host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, 
   s.gh[1] = s.glev[1] - gb[1];
 }
 
-// the values only (level deviation, depth, discharge) of cell c's layer-ell
-// reconstruction at scaled point (x, y) through transform xf
+// the level deviation and the discharges at scaled point (x, y) from a
+// loaded side record
 template <typename R>
-__host__ __device__ inline void side_values(const Dev &d, int ell, int c, int xf, R x, R y, R href, R &dv, R &h,
-                                            R &mx, R &my) {
-  R w[NREC];
-  load_rec<R, NREC>((const R *)d.srec + ((size_t)ell * d.cs + c) * NREC, w);
+__host__ __device__ __forceinline__ void rec_values(const R *w, R x, R y, R v[3]) {
   const R hh = (R)0.5, s6 = (R)(1.0 / 6.0);
   const R xx = x * x, yy = y * y, xy = x * y;
   const R m[10] = {(R)1, x, y, hh * xx, xy, hh * yy, xx * x * s6, hh * xx * y, hh * x * yy, yy * y * s6};
-  R v[3];
   for (int i = 0; i < 3; i++) {
     R a = w[12 * i] * m[0];
     for (int k = 1; k < 10; k++) a += w[12 * i + k] * m[k];
     v[i] = w[12 * i + 10] + a;
-  }
-  dv = v[0];
-  h = href + v[0];
-  mx = v[1];
-  my = v[2];
-  if (xf != 0) {
-    R mv[2] = {mx, my};
-    rot2<R>(d.xf + 4 * xf, mv);
-    mx = mv[0];
-    my = mv[1];
   }
 }
 
@@ -685,23 +671,40 @@ __host__ __device__ inline void gks_layer(R href, R dl, R dr, R Ul, R Vl, R Ur, 
 }
 
 // ---------------------------------------------------- interface (iface) unit
-// Blended level deviation at one Gauss point of edge e for layer ell
-// (Sec. 2.3): h-hat = xi h^l + (1 - xi) h^r, xi = erfc((U_n^l + U_n^r)/2)/2;
-// the lower layer is blended as the water level eta1 (B is continuous).
+// Blended level deviation of layer ell at edge e (Sec. 2.3), the mean over
+// the two Gauss points of h-hat = xi h^l + (1 - xi) h^r with
+// xi = erfc((U_n^l + U_n^r)/2)/2; the lower layer is blended as the water
+// level eta1 (B is continuous). Each side's record is loaded once for both
+// points.
 template <typename R>
-__host__ __device__ inline R iface_unit(const Dev &d, int e, int ell, int q) {
-  const int NE = d.ne;
+__host__ __device__ inline R iface_unit(const Dev &d, int e, int ell) {
+  const int NE = d.ne, N = d.cs;
   const R *xl = (const R *)d.exiL, *xr = (const R *)d.exiR, *en = (const R *)d.en;
-  int cL = d.eL[e], cR = d.eR[e], xf = d.exf[e];
-  const R href = ref_depth<R>(d, ell, e, q);
-  R dl, hl, mxl, myl, dr, hr, mxr, myr;
-  side_values<R>(d, ell, cL, 0, xl[(2 * q) * NE + e], xl[(2 * q + 1) * NE + e], href, dl, hl, mxl, myl);
-  side_values<R>(d, ell, cR, xf, xr[(2 * q) * NE + e], xr[(2 * q + 1) * NE + e], href, dr, hr, mxr, myr);
+  const int cL = d.eL[e], cR = d.eR[e], xf = d.exf[e];
+  R vl[2][3], vr[2][3];
+  {
+    R w[NREC];
+    load_rec<R, NREC>((const R *)d.srec + ((size_t)ell * N + cL) * NREC, w);
+    for (int q = 0; q < 2; q++) rec_values<R>(w, xl[(2 * q) * NE + e], xl[(2 * q + 1) * NE + e], vl[q]);
+  }
+  {
+    R w[NREC];
+    load_rec<R, NREC>((const R *)d.srec + ((size_t)ell * N + cR) * NREC, w);
+    for (int q = 0; q < 2; q++) rec_values<R>(w, xr[(2 * q) * NE + e], xr[(2 * q + 1) * NE + e], vr[q]);
+  }
   const R n0 = en[e], n1 = en[NE + e];
-  R ul = (mxl * n0 + myl * n1) / hl;
-  R ur = (mxr * n0 + myr * n1) / hr;
-  R xi = (R)0.5 * r_erfc<R>((R)0.5 * (ul + ur));
-  return dr + xi * (dl - dr);
+  R s = 0;
+  for (int q = 0; q < 2; q++) {
+    R mr[2] = {vr[q][1], vr[q][2]};
+    if (xf != 0) rot2<R>(d.xf + 4 * xf, mr);
+    const R href = ref_depth<R>(d, ell, e, q);
+    const R dl = vl[q][0], dr = vr[q][0];
+    const R ul = (vl[q][1] * n0 + vl[q][2] * n1) / (href + dl);
+    const R ur = (mr[0] * n0 + mr[1] * n1) / (href + dr);
+    const R xi = (R)0.5 * r_erfc<R>((R)0.5 * (ul + ur));
+    s += dr + xi * (dl - dr);
+  }
+  return (R)0.5 * s;
 }
 
 // plane gradient (Sec. 2.3) of the blended level `which` for cell c
