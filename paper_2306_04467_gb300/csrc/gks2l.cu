@@ -268,7 +268,7 @@ __device__ __forceinline__ void iface_body(const Dev &d) {
   ((R *)d.hc)[ell * d.ne + e] = iface_unit<R>(d, e, ell);
 }
 
-template <typename R>
+template <typename R, bool G>
 __device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   int e = tid >> 2, ell = (tid >> 1) & 1, q = tid & 1;
@@ -277,7 +277,7 @@ __device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage)
   ok = ok && d.dt[d.inst[d.eL[ee]]] > 0;
   R out[12];
   if (ok) {
-    edge_unit<R>(d, p, ee, ell, q, stage, out);
+    edge_unit<R, G>(d, p, ee, ell, q, stage, out);
   } else {
     for (int k = 0; k < 12; k++) out[k] = 0;
   }
@@ -370,20 +370,20 @@ __device__ __forceinline__ void update_body(const Dev &d, const Par &p, int stag
 
 template <typename R, int BS>
 __global__ void __launch_bounds__(BS) k_iface(Dev d) { iface_body<R>(d); }
-template <typename R, int BS>
-__global__ void __launch_bounds__(BS) k_edge(Dev d, Par p, int stage) { edge_body<R>(d, p, stage); }
+template <typename R, int BS, bool G>
+__global__ void __launch_bounds__(BS) k_edge(Dev d, Par p, int stage) { edge_body<R, G>(d, p, stage); }
 template <typename R, int BS>
 __global__ void __launch_bounds__(BS) k_update(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
 template <typename R>
 __global__ void __launch_bounds__(128, 8) k_iface_r64(Dev d) { iface_body<R>(d); }
-template <typename R>
-__global__ void __launch_bounds__(128, 8) k_edge_r64(Dev d, Par p, int stage) { edge_body<R>(d, p, stage); }
+template <typename R, bool G>
+__global__ void __launch_bounds__(128, 8) k_edge_r64(Dev d, Par p, int stage) { edge_body<R, G>(d, p, stage); }
 template <typename R>
 __global__ void __launch_bounds__(128, 8) k_update_r64(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
 template <typename R>
 __global__ void __launch_bounds__(128, 4) k_iface_r128(Dev d) { iface_body<R>(d); }
-template <typename R>
-__global__ void __launch_bounds__(128, 4) k_edge_r128(Dev d, Par p, int stage) { edge_body<R>(d, p, stage); }
+template <typename R, bool G>
+__global__ void __launch_bounds__(128, 4) k_edge_r128(Dev d, Par p, int stage) { edge_body<R, G>(d, p, stage); }
 template <typename R>
 __global__ void __launch_bounds__(128, 4) k_update_r128(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
 
@@ -752,6 +752,15 @@ constexpr int kShapes = 5;
     case 4: KERNEL##_r128<R><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;           \
     default: KERNEL<R, 128><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;            \
   }
+// the same for a kernel with one more (bool) template argument
+#define GKS2L_SHAPE_SWITCH_B(cfg, KERNEL, B, n, st, ...)                                     \
+  switch (cfg) {                                                                           \
+    case 0: KERNEL<R, 64, B><<<blocks(n, 64), 64, 0, st>>>(__VA_ARGS__); break;             \
+    case 2: KERNEL<R, 256, B><<<blocks(n, 256), 256, 0, st>>>(__VA_ARGS__); break;          \
+    case 3: KERNEL##_r64<R, B><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;         \
+    case 4: KERNEL##_r128<R, B><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;        \
+    default: KERNEL<R, 128, B><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;         \
+  }
 
 template <typename R>
 void launch_iface(gks2l_ctx *c, cudaStream_t st) {
@@ -762,7 +771,11 @@ void launch_iface(gks2l_ctx *c, cudaStream_t st) {
 template <typename R>
 void launch_edge(gks2l_ctx *c, const Par &p, int stage, cudaStream_t st) {
   const size_t n = 4 * (size_t)c->d.ne;
-  GKS2L_SHAPE_SWITCH(c->shape[1], k_edge, n, st, c->d, p, stage)
+  if (p.use_gate) {
+    GKS2L_SHAPE_SWITCH_B(c->shape[1], k_edge, true, n, st, c->d, p, stage)
+  } else {
+    GKS2L_SHAPE_SWITCH_B(c->shape[1], k_edge, false, n, st, c->d, p, stage)
+  }
 }
 
 template <typename R>

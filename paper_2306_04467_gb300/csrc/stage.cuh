@@ -725,7 +725,11 @@ __host__ __device__ __forceinline__ void plane_grad(const Dev &d, int c, int whi
 // ------------------------------------------------------------- edge unit
 // Interface solution of layer ell at Gauss point q of edge e, global frame:
 // out[0..2] = F, out[3..5] = F_t, out[6..8] = W, out[9..11] = W_t (deviations).
-template <typename R>
+// With SKIP_PLANE (runs with the troubled-cell gate, where most cells take
+// the linear weights) the plane gradients are gathered only where their
+// weight 1 - w is nonzero; without it they are gathered unconditionally,
+// which lets their loads issue with the others.
+template <typename R, bool SKIP_PLANE = false>
 __host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int ell, int q, int stage, R out[12]) {
   const int NE = d.ne;
   const R *xl = (const R *)d.exiL, *xr = (const R *)d.exiR, *en = (const R *)d.en;
@@ -742,10 +746,14 @@ __host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int
   const R *om = (const R *)d.omg;
   R w = om[oth * d.cs + cL] < om[oth * d.cs + cR] ? om[oth * d.cs + cL] : om[oth * d.cs + cR];
   w = w < (R)0 ? (R)0 : (w > (R)1 ? (R)1 : w);
-  R pl[2][2];
-  plane_grad<R>(d, cL, oth, pl[0]);
-  plane_grad<R>(d, cR, oth, pl[1]);
-  if (xf != 0) rot2<R>(d.xf + 4 * xf, pl[1]);
+  // the plane gradients enter with weight 1 - w: where both cells took the
+  // linear weights (w = 1) they drop out
+  R pl[2][2] = {{0, 0}, {0, 0}};
+  if (!SKIP_PLANE || w < (R)1) {
+    plane_grad<R>(d, cL, oth, pl[0]);
+    plane_grad<R>(d, cR, oth, pl[1]);
+    if (xf != 0) rot2<R>(d.xf + 4 * xf, pl[1]);
+  }
   const R cf = ell == 0 ? pv<R>(p.chi, p.chif) : (R)1;
   const R n0 = en[e], n1 = en[NE + e];
   R U[2], V[2], dn[2][3], dtt[2][3], D[2][2];
