@@ -129,6 +129,9 @@ __global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p)
     bulk_load(sm, src, T::TX_LINEAR, bar);
     if (!all_linear) bulk_load(sm + T::P1, src + T::P1, T::TX - T::TX_LINEAR, bar);
   }
+  // the cell's activity (a chain of two loads) resolves during the copies
+  const int j = j0 + threadIdx.x, v = threadIdx.y;
+  const bool active = j < d.nt && (p.all_active || d.dt[d.inst[j]] > 0);
   __syncthreads();
   const bool landed = mbar_wait_bounded(bar, 0, 1000000000ull);
   if (!__syncthreads_and(landed)) {
@@ -138,8 +141,6 @@ __global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p)
     if (!landed) mbar_wait_bounded(bar, 0, 1000000000ull);
     return;
   }
-  const int j = j0 + threadIdx.x, v = threadIdx.y;
-  const bool active = j < d.nt && (p.all_active || d.dt[d.inst[j]] > 0);
   CellOps<R> o;
   o.lsq = (const R *)(sm + T::LSQ);
   o.p1 = (const R *)(sm + T::P1);
@@ -272,15 +273,13 @@ template <typename R, bool G>
 __device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   int e = tid >> 2, ell = (tid >> 1) & 1, q = tid & 1;
-  bool ok = e < d.ne;
-  int ee = ok ? e : d.ne - 1;
-  ok = ok && d.dt[d.inst[d.eL[ee]]] > 0;
+  const int ee = e < d.ne ? e : d.ne - 1;
+  // every thread computes (past the last edge: the last edge again), before
+  // its instance's dt is known, so the unit's loads issue at once; only
+  // edges of instances still running are written
   R out[12];
-  if (ok) {
-    edge_unit<R, G>(d, p, ee, ell, q, stage, out);
-  } else {
-    for (int k = 0; k < 12; k++) out[k] = 0;
-  }
+  edge_unit<R, G>(d, p, ee, ell, q, stage, out);
+  const bool ok = e < d.ne && d.dt[d.inst[d.eL[ee]]] > 0;
   // the Gauss point q = 0 thread averages the fluxes (out[0..5]), the q = 1
   // thread the interface values (out[6..11]): each sends the other its half
   R avg[6];

@@ -803,7 +803,9 @@ __host__ __device__ inline double update_unit(const Dev &d, const Par &p, int j,
   const int N = d.cs, NE = d.ne;
   const int in = d.inst[j];
   const double dt = d.dt[in];
-  if (!(dt > 0)) return 0;
+  // the unit's loads and arithmetic do not wait on dt: a cell of an instance
+  // that has stopped (dt = 0) is computed too, and only its writes are dropped
+  const bool act = dt > 0;
   const R *eF = (const R *)d.eF, *eFt = (const R *)d.eFt, *eWt = (const R *)d.eWt, *eWn = (const R *)d.eWn;
   const R *Wcur = stage == 1 ? eWn : (const R *)d.eW;
   const R *en = (const R *)d.en;
@@ -863,31 +865,35 @@ __host__ __device__ inline double update_unit(const Dev &d, const Par &p, int j,
   for (int v = 0; v < NV; v++) {
     double a = d.avg[v * N + j];
     if (stage == 1) {
-      d.Wn[v * N + j] = a;
-      d.Ln[v * N + j] = Ld[v];
-      d.Ltn[v * N + j] = Ltd[v];
+      if (act) {
+        d.Wn[v * N + j] = a;
+        d.Ln[v * N + j] = Ld[v];
+        d.Ltn[v * N + j] = Ltd[v];
+      }
       nw[v] = a + 0.5 * dt * Ld[v] + 0.125 * dt * dt * Ltd[v];
     } else {
       nw[v] = d.Wn[v * N + j] + dt * d.Ln[v * N + j] + dt * dt * (1.0 / 6.0) * d.Ltn[v * N + j] +
               dt * dt * (1.0 / 3.0) * Ltd[v];
     }
   }
-  R *dqw = (R *)d.dq, *dgw = (R *)d.dg;
-  for (int v = 0; v < NV; v++) {
-    d.avg[v * N + j] = nw[v];
-    dgw[(2 * v) * N + j] = GGn[v][0];
-    dgw[(2 * v + 1) * N + j] = GGn[v][1];
+  if (act) {
+    R *dqw = (R *)d.dq, *dgw = (R *)d.dg;
+    for (int v = 0; v < NV; v++) {
+      d.avg[v * N + j] = nw[v];
+      dgw[(2 * v) * N + j] = GGn[v][0];
+      dgw[(2 * v + 1) * N + j] = GGn[v][1];
+    }
+    dqw[j] = (R)(nw[0] - d.ref[2 * in]);
+    dqw[3 * N + j] = (R)((nw[3] + d.bmean[j]) - d.ref[2 * in + 1]);
+    for (int i = 0; i < 4; i++) dqw[mom[i] * N + j] = (R)nw[mom[i]];
   }
-  dqw[j] = (R)(nw[0] - d.ref[2 * in]);
-  dqw[3 * N + j] = (R)((nw[3] + d.bmean[j]) - d.ref[2 * in + 1]);
-  for (int i = 0; i < 4; i++) dqw[mom[i] * N + j] = (R)nw[mom[i]];
   // health flags by integer tests on the bits (off the FP64 pipe)
   int fl = 0;
   for (int v = 0; v < NV; v++)
     if (!finite_bits(nw[v]) || !isfinite(GGn[v][0]) || !isfinite(GGn[v][1])) fl |= 2;
   if (!(dbits(nw[0]) > 0) || !(dbits(nw[3]) > 0)) fl |= 1;
-  *flags = fl;
-  if (stage != 2) return 0;
+  *flags = act ? fl : 0;
+  if (stage != 2 || !act) return 0;
   R um = 0;
   for (int l = 0; l < 2; l++) {
     R h = (R)nw[3 * l], u = (R)nw[3 * l + 1] / h, v = (R)nw[3 * l + 2] / h;
