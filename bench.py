@@ -51,12 +51,13 @@ N_SQ = 1024
 # side records out, without the P1 and smoothness rows for gated tiles; gate:
 # 3 neighbour ids and transforms, eta1/h2 values and gradients, scales;
 # interface: edge geometry, both cells' side records, two levels out; edge:
-# the same plus plane rows and blend weights, 24 interface values out;
+# the same plus blend weights, 24 interface values out, without the plane rows
+# the gate makes unnecessary on this workload;
 # update: three edges' fluxes and interface values, state in/out with the
 # S2O4 snapshot, mirrors out). Units: cells for recon, gate and update, edges for iface and edge.
 WORK_PER_UNIT = {
-    "fp32": {"recon": (2196, 0, 1069), "gate": (280, 0, 51), "iface": (906, 0, 265), "edge": (6239, 0, 374),
-             "update": (332, 61, 570)},
+    "fp32": {"recon": (2196, 0, 1069), "gate": (257, 0, 51), "iface": (836, 0, 265), "edge": (5405, 0, 342),
+             "update": (298, 61, 570)},
     "fp64": {"recon": (69, 4593, 2209), "gate": (280, 0, 63), "iface": (15, 1349, 473), "edge": (107, 9162, 696),
              "update": (0, 343, 850)},
 }
@@ -64,7 +65,7 @@ WORK_PER_UNIT = {
 PEAK_TFLOPS = {"fp32": 76.5, "fp64": 1.254}
 # DRAM bytes per unit (dram__bytes_read.sum + dram__bytes_write.sum of the
 # same launches, per unit; inputs larger than L2, traffic grows with units).
-TRAFFIC_PER_UNIT = {"fp32": {"recon": 1023.0, "gate": 51.0, "iface": 260.0, "edge": 362.0, "update": 456.0}}
+TRAFFIC_PER_UNIT = {"fp32": {"recon": 1028.0, "gate": 51.0, "iface": 259.0, "edge": 327.0, "update": 455.0}}
 
 
 def roofline(form, kernel, units, ms, hbm_gbs):
