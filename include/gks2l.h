@@ -216,7 +216,8 @@ int gks2l_mlp_forward(const float *d_X, int32_t n, const float *d_params, float 
 
 /* ---- launch shapes (not part of the paper) --------------------------------
  * The interface, edge and update kernels each run in one of five launch
- * shapes: 0: 64 threads per block, 1: 128 (default), 2: 256, 3: 128 threads
+ * shapes (with the gate on, the edge shape applies to the fused interface and
+ * edge kernel): 0: 64 threads per block, 1: 128 (default), 2: 256, 3: 128 threads
  * held to 64 registers (eight blocks per SM), 4: 128 threads held to 128
  * registers (four blocks per SM). Results do not depend on them. */
 #define GKS2L_LAUNCH_SHAPES 5
@@ -235,7 +236,10 @@ int gks2l_autotune(gks2l_ctx *ctx, int32_t n_steps, int32_t shapes[3]);
  * the mean duration of one launch of kernel k, in the order: reconstruction,
  * interface levels, edge solution, cell update (each averaged over both
  * stages), step start, troubled-cell gate (0 when it is off; run here in
- * sequence, in gks2l_advance beside the interface and edge kernels).
+ * sequence, in gks2l_advance beside the edge kernels). With the gate on, the
+ * interface levels and the edge solution run as one fused kernel, reported
+ * in the edge slot, followed by a pass over the edges whose solution needs
+ * the plane gradients, reported in the interface slot.
  * Requires a state and phase at a step boundary. */
 int gks2l_profile_kernels(gks2l_ctx *ctx, int32_t n_steps, double ms[6]);
 

@@ -269,7 +269,7 @@ __device__ __forceinline__ void iface_body(const Dev &d) {
   ((R *)d.hc)[ell * d.ne + e] = iface_unit<R>(d, e, ell);
 }
 
-template <typename R, bool G>
+template <typename R>
 __device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   int e = tid >> 2, ell = (tid >> 1) & 1, q = tid & 1;
@@ -278,7 +278,7 @@ __device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage)
   // its instance's dt is known, so the unit's loads issue at once; only
   // edges of instances still running are written
   R out[12];
-  edge_unit<R, G>(d, p, ee, ell, q, stage, out);
+  edge_unit<R>(d, p, ee, ell, q, stage, out);
   const bool ok = e < d.ne && d.dt[d.inst[d.eL[ee]]] > 0;
   // the Gauss point q = 0 thread averages the fluxes (out[0..5]), the q = 1
   // thread the interface values (out[6..11]): each sends the other its half
@@ -296,6 +296,88 @@ __device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage)
   for (int k = 0; k < 3; k++) {
     A[(vb + k) * NE + e] = avg[k];
     B[(vb + k) * NE + e] = avg[3 + k];
+  }
+}
+
+// Gated runs: the interface levels and the edge solution in one kernel. Each
+// (edge, layer, point) thread evaluates both sides once, forms the point's
+// blended level (the pair's mean is the edge's, written to hc) and, where the
+// blend weight is 1, the solution; the other (edge, layer) units go to the
+// worklist for k_edge_deferred, which runs once every blended level exists.
+template <typename R>
+__device__ __forceinline__ void edge_fused_body(const Dev &d, const Par &p, int stage) {
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = tid >> 2, ell = (tid >> 1) & 1, q = tid & 1;
+  const int ee = e < d.ne ? e : d.ne - 1;
+  R out[12], bl = 0;
+  const bool done = edge_unit<R, true>(d, p, ee, ell, q, stage, out, &bl);
+  if (!done) {
+    for (int k = 0; k < 12; k++) out[k] = 0;
+  }
+  // the edge's blended level: the mean over its two points, summed in point
+  // order as the interface kernel sums it
+  const R bo = __shfl_xor_sync(FULL, bl, 1);
+  const R hcv = Rn<R>::mul((R)0.5, q == 0 ? Rn<R>::add(bl, bo) : Rn<R>::add(bo, bl));
+  R avg[6];
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const R mine = q == 0 ? out[k] : out[6 + k], theirs = q == 0 ? out[6 + k] : out[k];
+    avg[k] = (R)0.5 * (mine + __shfl_xor_sync(FULL, theirs, 1));
+  }
+  const bool ok = e < d.ne && d.dt[d.inst[d.eL[ee]]] > 0;
+  // deferred units to the worklist, one atomic per warp
+  const bool push = ok && q == 0 && !done;
+  const unsigned bal = __ballot_sync(FULL, push);
+  if (bal) {
+    const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(d.wl_count, __popc(bal));
+    base = __shfl_sync(FULL, base, leader);
+    if (push) d.wl[base + __popc(bal & ((1u << lane) - 1u))] = (e << 1) | ell;
+  }
+  if (!ok) return;
+  const int NE = d.ne;
+  if (q == 0) ((R *)d.hc)[ell * NE + e] = hcv;
+  if (!done) return;
+  const int vb = ell == 0 ? 3 : 0;
+  R *A = (R *)(q == 0 ? d.eF : (stage == 1 ? d.eWn : d.eW));
+  R *B = (R *)(q == 0 ? d.eFt : d.eWt);
+  for (int k = 0; k < 3; k++) {
+    A[(vb + k) * NE + e] = avg[k];
+    B[(vb + k) * NE + e] = avg[3 + k];
+  }
+}
+
+// The worklist's units with the plane gradients (every blended level is
+// written by now): warps walk it 16 units at a time, a thread pair per unit.
+constexpr int DEFER_BLOCKS_PER_SM = 4;
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_edge_deferred(Dev d, Par p, int stage) {
+  const int n = *d.wl_count;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarp = (gridDim.x * blockDim.x) >> 5;
+  const int NE = d.ne;
+  for (int base = warp * 16; base < n; base += nwarp * 16) {
+    const int i = base + (lane >> 1), q = lane & 1;
+    const int item = d.wl[i < n ? i : n - 1];
+    const int e = item >> 1, ell = item & 1;
+    R out[12];
+    edge_unit<R>(d, p, e, ell, q, stage, out);
+    R avg[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const R mine = q == 0 ? out[k] : out[6 + k], theirs = q == 0 ? out[6 + k] : out[k];
+      avg[k] = (R)0.5 * (mine + __shfl_xor_sync(FULL, theirs, 1));
+    }
+    if (i >= n) continue;
+    const int vb = ell == 0 ? 3 : 0;
+    R *A = (R *)(q == 0 ? d.eF : (stage == 1 ? d.eWn : d.eW));
+    R *B = (R *)(q == 0 ? d.eFt : d.eWt);
+    for (int k = 0; k < 3; k++) {
+      A[(vb + k) * NE + e] = avg[k];
+      B[(vb + k) * NE + e] = avg[3 + k];
+    }
   }
 }
 
@@ -369,20 +451,26 @@ __device__ __forceinline__ void update_body(const Dev &d, const Par &p, int stag
 
 template <typename R, int BS>
 __global__ void __launch_bounds__(BS) k_iface(Dev d) { iface_body<R>(d); }
-template <typename R, int BS, bool G>
-__global__ void __launch_bounds__(BS) k_edge(Dev d, Par p, int stage) { edge_body<R, G>(d, p, stage); }
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_edge(Dev d, Par p, int stage) { edge_body<R>(d, p, stage); }
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_edgef(Dev d, Par p, int stage) { edge_fused_body<R>(d, p, stage); }
 template <typename R, int BS>
 __global__ void __launch_bounds__(BS) k_update(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
 template <typename R>
 __global__ void __launch_bounds__(128, 8) k_iface_r64(Dev d) { iface_body<R>(d); }
-template <typename R, bool G>
-__global__ void __launch_bounds__(128, 8) k_edge_r64(Dev d, Par p, int stage) { edge_body<R, G>(d, p, stage); }
+template <typename R>
+__global__ void __launch_bounds__(128, 8) k_edge_r64(Dev d, Par p, int stage) { edge_body<R>(d, p, stage); }
+template <typename R>
+__global__ void __launch_bounds__(128, 8) k_edgef_r64(Dev d, Par p, int stage) { edge_fused_body<R>(d, p, stage); }
 template <typename R>
 __global__ void __launch_bounds__(128, 8) k_update_r64(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
 template <typename R>
 __global__ void __launch_bounds__(128, 4) k_iface_r128(Dev d) { iface_body<R>(d); }
-template <typename R, bool G>
-__global__ void __launch_bounds__(128, 4) k_edge_r128(Dev d, Par p, int stage) { edge_body<R, G>(d, p, stage); }
+template <typename R>
+__global__ void __launch_bounds__(128, 4) k_edge_r128(Dev d, Par p, int stage) { edge_body<R>(d, p, stage); }
+template <typename R>
+__global__ void __launch_bounds__(128, 4) k_edgef_r128(Dev d, Par p, int stage) { edge_fused_body<R>(d, p, stage); }
 template <typename R>
 __global__ void __launch_bounds__(128, 4) k_update_r128(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
 
@@ -604,6 +692,8 @@ size_t layout(gks2l_ctx *c, char *base) {
   d.exiR = k.take<char>(rs * 4 * ne);
   d.hrefe = k.take<char>(rs * 2 * ne);
   d.hc = k.take<char>(rs * 2 * ne);
+  d.wl = k.take<int>(2 * ne);
+  d.wl_count = k.take<int>(1);
   d.eF = k.take<char>(rs * 6 * ne);
   d.eFt = k.take<char>(rs * 6 * ne);
   d.eW = k.take<char>(rs * 6 * ne);
@@ -751,15 +841,6 @@ constexpr int kShapes = 5;
     case 4: KERNEL##_r128<R><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;           \
     default: KERNEL<R, 128><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;            \
   }
-// the same for a kernel with one more (bool) template argument
-#define GKS2L_SHAPE_SWITCH_B(cfg, KERNEL, B, n, st, ...)                                     \
-  switch (cfg) {                                                                           \
-    case 0: KERNEL<R, 64, B><<<blocks(n, 64), 64, 0, st>>>(__VA_ARGS__); break;             \
-    case 2: KERNEL<R, 256, B><<<blocks(n, 256), 256, 0, st>>>(__VA_ARGS__); break;          \
-    case 3: KERNEL##_r64<R, B><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;         \
-    case 4: KERNEL##_r128<R, B><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;        \
-    default: KERNEL<R, 128, B><<<blocks(n, 128), 128, 0, st>>>(__VA_ARGS__); break;         \
-  }
 
 template <typename R>
 void launch_iface(gks2l_ctx *c, cudaStream_t st) {
@@ -770,11 +851,19 @@ void launch_iface(gks2l_ctx *c, cudaStream_t st) {
 template <typename R>
 void launch_edge(gks2l_ctx *c, const Par &p, int stage, cudaStream_t st) {
   const size_t n = 4 * (size_t)c->d.ne;
-  if (p.use_gate) {
-    GKS2L_SHAPE_SWITCH_B(c->shape[1], k_edge, true, n, st, c->d, p, stage)
-  } else {
-    GKS2L_SHAPE_SWITCH_B(c->shape[1], k_edge, false, n, st, c->d, p, stage)
-  }
+  GKS2L_SHAPE_SWITCH(c->shape[1], k_edge, n, st, c->d, p, stage)
+}
+
+// gated runs: interface levels and edge solution fused, then the deferred units
+template <typename R>
+void launch_edge_fused(gks2l_ctx *c, const Par &p, int stage, cudaStream_t st) {
+  const size_t n = 4 * (size_t)c->d.ne;
+  cudaMemsetAsync(c->d.wl_count, 0, sizeof(int), st);
+  GKS2L_SHAPE_SWITCH(c->shape[1], k_edgef, n, st, c->d, p, stage)
+}
+template <typename R>
+void launch_edge_deferred(gks2l_ctx *c, const Par &p, int stage, cudaStream_t st) {
+  k_edge_deferred<R><<<c->n_sm * DEFER_BLOCKS_PER_SM, 128, 0, st>>>(c->d, p, stage);
 }
 
 template <typename R>
@@ -789,14 +878,19 @@ void launch_stage(gks2l_ctx *c, int stage) {
   launch_recon<R>(c, p);
   if (p.use_gate) {
     // the gate for the next stage reads this stage's state, which k_update
-    // replaces: it runs beside k_iface and k_edge and joins before k_update
+    // replaces: it runs beside the edge kernels and joins before k_update
     cudaEventRecord(c->ev_fork, c->stream);
     cudaStreamWaitEvent(c->side, c->ev_fork, 0);
     launch_gate<R>(c, p, c->side);
     cudaEventRecord(c->ev_join, c->side);
   }
-  launch_iface<R>(c, c->stream);
-  launch_edge<R>(c, p, stage, c->stream);
+  if (p.use_gate) {
+    launch_edge_fused<R>(c, p, stage, c->stream);
+    launch_edge_deferred<R>(c, p, stage, c->stream);
+  } else {
+    launch_iface<R>(c, c->stream);
+    launch_edge<R>(c, p, stage, c->stream);
+  }
   if (p.use_gate) cudaStreamWaitEvent(c->stream, c->ev_join, 0);
   launch_update<R>(c, p, stage, c->stream);
 }
@@ -1174,12 +1268,25 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[6]) {
         if (f32) launch_gate<float>(c, p, c->stream);
         else launch_gate<double>(c, p, c->stream);
       }
+      // ungated: interface kernel between ev[7] and ev[4], edge kernel up to
+      // ev[5]; gated: fused kernel between ev[7] and ev[4] (reported as the
+      // edge time), deferred pass up to ev[5] (reported in the interface slot)
       CK(cudaEventRecord(ev[7], c->stream));
-      if (f32) launch_iface<float>(c, c->stream);
-      else launch_iface<double>(c, c->stream);
+      if (p.use_gate) {
+        if (f32) launch_edge_fused<float>(c, p, stage, c->stream);
+        else launch_edge_fused<double>(c, p, stage, c->stream);
+      } else {
+        if (f32) launch_iface<float>(c, c->stream);
+        else launch_iface<double>(c, c->stream);
+      }
       CK(cudaEventRecord(ev[4], c->stream));
-      if (f32) launch_edge<float>(c, p, stage, c->stream);
-      else launch_edge<double>(c, p, stage, c->stream);
+      if (p.use_gate) {
+        if (f32) launch_edge_deferred<float>(c, p, stage, c->stream);
+        else launch_edge_deferred<double>(c, p, stage, c->stream);
+      } else {
+        if (f32) launch_edge<float>(c, p, stage, c->stream);
+        else launch_edge<double>(c, p, stage, c->stream);
+      }
       CK(cudaEventRecord(ev[5], c->stream));
       if (f32) launch_update<float>(c, p, stage, c->stream);
       else launch_update<double>(c, p, stage, c->stream);
@@ -1191,11 +1298,11 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[6]) {
       CK(cudaEventElapsedTime(&t, ev[3], ev[7]));
       acc[5] += t;
       CK(cudaEventElapsedTime(&t, ev[7], ev[4]));
-      acc[1] += t;
-      for (int k = 2; k < 4; k++) {
-        CK(cudaEventElapsedTime(&t, ev[2 + k], ev[3 + k]));
-        acc[k] += t;
-      }
+      acc[p.use_gate ? 2 : 1] += t;
+      CK(cudaEventElapsedTime(&t, ev[4], ev[5]));
+      acc[p.use_gate ? 1 : 2] += t;
+      CK(cudaEventElapsedTime(&t, ev[5], ev[6]));
+      acc[3] += t;
     }
     float t0;
     CK(cudaEventElapsedTime(&t0, ev[0], ev[1]));

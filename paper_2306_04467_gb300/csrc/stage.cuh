@@ -83,6 +83,8 @@ struct Dev {
   const void *exiL, *exiR;  // [4][edge] Gauss points in each side's scaled frame, type R
   void *hrefe;              // [2][edge] R1 - B at the Gauss points, type R
   void *hc;                 // [2][edge] edge-centre blended level deviations, type R
+  int *wl;                  // [2 * edge] (edge << 1 | layer) units left to the deferred edge pass
+  int *wl_count;            // their number (zeroed before each fused edge launch)
   void *eF, *eFt, *eW, *eWt, *eWn;  // [6][edge] Gauss-point sums (weights 1/2), deviations, type R
   // per instance
   double *ref;              // [inst*2]: R2, R1
@@ -670,6 +672,51 @@ __host__ __device__ inline void gks_layer(R href, R dl, R dr, R Ul, R Vl, R Ur, 
   for (int k = 0; k < 3; k++) { Wt[k] = wt[k]; Ft[k] = ft[k]; }
 }
 
+// Blended level deviation at one point (Sec. 2.3): d^r + xi (d^l - d^r) with
+// xi = erfc((U_n^l + U_n^r)/2)/2, U_n = (m . n) / h on each side. Written
+// with explicitly rounded operations so that the interface kernel and the
+// fused edge kernel, which both form it, get the same value whatever the
+// compiler does with the code around it.
+template <typename R> struct Rn;
+template <> struct Rn<float> {
+#ifdef __CUDA_ARCH__
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+#else
+  static float mul(float a, float b) { return a * b; }
+  static float add(float a, float b) { return a + b; }
+  static float sub(float a, float b) { return a - b; }
+  static float fma(float a, float b, float c) { return std::fma(a, b, c); }
+  static float rcp(float a) { return 1.0f / a; }
+#endif
+};
+template <> struct Rn<double> {
+#ifdef __CUDA_ARCH__
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+  static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
+#else
+  static double mul(double a, double b) { return a * b; }
+  static double add(double a, double b) { return a + b; }
+  static double sub(double a, double b) { return a - b; }
+  static double fma(double a, double b, double c) { return std::fma(a, b, c); }
+  static double rcp(double a) { return 1.0 / a; }
+#endif
+};
+template <typename R>
+__host__ __device__ __forceinline__ R blend_level(R dl, R hl, R mxl, R myl, R dr, R hr, R mxr, R myr, R n0, R n1) {
+  using O = Rn<R>;
+  const R ul = O::mul(O::fma(mxl, n0, O::mul(myl, n1)), O::rcp(hl));
+  const R ur = O::mul(O::fma(mxr, n0, O::mul(myr, n1)), O::rcp(hr));
+  const R xi = O::mul((R)0.5, r_erfc<R>(O::mul((R)0.5, O::add(ul, ur))));
+  return O::fma(xi, O::sub(dl, dr), dr);
+}
+
 // ---------------------------------------------------- interface (iface) unit
 // Blended level deviation of layer ell at edge e (Sec. 2.3), the mean over
 // the two Gauss points of h-hat = xi h^l + (1 - xi) h^r with
@@ -693,18 +740,15 @@ __host__ __device__ inline R iface_unit(const Dev &d, int e, int ell) {
     for (int q = 0; q < 2; q++) rec_values<R>(w, xr[(2 * q) * NE + e], xr[(2 * q + 1) * NE + e], vr[q]);
   }
   const R n0 = en[e], n1 = en[NE + e];
-  R s = 0;
+  R v[2];
   for (int q = 0; q < 2; q++) {
     R mr[2] = {vr[q][1], vr[q][2]};
     if (xf != 0) rot2<R>(d.xf + 4 * xf, mr);
     const R href = ref_depth<R>(d, ell, e, q);
     const R dl = vl[q][0], dr = vr[q][0];
-    const R ul = (vl[q][1] * n0 + vl[q][2] * n1) / (href + dl);
-    const R ur = (mr[0] * n0 + mr[1] * n1) / (href + dr);
-    const R xi = (R)0.5 * r_erfc<R>((R)0.5 * (ul + ur));
-    s += dr + xi * (dl - dr);
+    v[q] = blend_level<R>(dl, href + dl, vl[q][1], vl[q][2], dr, href + dr, mr[0], mr[1], n0, n1);
   }
-  return (R)0.5 * s;
+  return Rn<R>::mul((R)0.5, Rn<R>::add(v[0], v[1]));
 }
 
 // plane gradient (Sec. 2.3) of the blended level `which` for cell c
@@ -725,12 +769,19 @@ __host__ __device__ __forceinline__ void plane_grad(const Dev &d, int c, int whi
 // ------------------------------------------------------------- edge unit
 // Interface solution of layer ell at Gauss point q of edge e, global frame:
 // out[0..2] = F, out[3..5] = F_t, out[6..8] = W, out[9..11] = W_t (deviations).
-// With SKIP_PLANE (runs with the troubled-cell gate, where most cells take
-// the linear weights) the plane gradients are gathered only where their
-// weight 1 - w is nonzero; without it they are gathered unconditionally,
-// which lets their loads issue with the others.
-template <typename R, bool SKIP_PLANE = false>
-__host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int ell, int q, int stage, R out[12]) {
+// Returns true when out was computed.
+// FUSED (runs with the troubled-cell gate, where most cells take the linear
+// weights): the unit also returns in *blend the point's blended level
+// deviation of layer ell, h-hat - href = d^r + xi (d^l - d^r) with
+// xi = erfc((U_n^l + U_n^r)/2)/2 (Sec. 2.3; the edge's blended level is the
+// mean over its two points), and computes the solution only where the blend
+// weight w of the other layer is 1, where the plane gradients, which need
+// every blended level of both cells, carry no weight; elsewhere it returns
+// false and the solution is left to a later pass (plain mode, plane
+// gradients gathered).
+template <typename R, bool FUSED = false>
+__host__ __device__ inline bool edge_unit(const Dev &d, const Par &p, int e, int ell, int q, int stage, R out[12],
+                                          R *blend = nullptr) {
   const int NE = d.ne;
   const R *xl = (const R *)d.exiL, *xr = (const R *)d.exiR, *en = (const R *)d.en;
   int cL = d.eL[e], cR = d.eR[e], xf = d.exf[e];
@@ -746,10 +797,10 @@ __host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int
   const R *om = (const R *)d.omg;
   R w = om[oth * d.cs + cL] < om[oth * d.cs + cR] ? om[oth * d.cs + cL] : om[oth * d.cs + cR];
   w = w < (R)0 ? (R)0 : (w > (R)1 ? (R)1 : w);
-  // the plane gradients enter with weight 1 - w: where both cells took the
-  // linear weights (w = 1) they drop out
+  // the plane gradients enter with weight 1 - w (the fused mode computes
+  // only units with w = 1)
   R pl[2][2] = {{0, 0}, {0, 0}};
-  if (!SKIP_PLANE || w < (R)1) {
+  if (!FUSED) {
     plane_grad<R>(d, cL, oth, pl[0]);
     plane_grad<R>(d, cR, oth, pl[1]);
     if (xf != 0) rot2<R>(d.xf + 4 * xf, pl[1]);
@@ -779,6 +830,10 @@ __host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int
       outv[k][2] = -dmx * n1 + dmy * n0;
     }
   }
+  if (FUSED) {
+    *blend = blend_level<R>(s[0].d, s[0].h, s[0].mx, s[0].my, s[1].d, s[1].h, s[1].mx, s[1].my, n0, n1);
+    if (w < (R)1) return false;
+  }
   // collision time (Sec. 4): tau = eps dt + eps_num |(hl^2 - hr^2)/(hl^2 + hr^2)| dt
   const R hl = s[0].h, hr = s[1].h;
   const R jump = r_abs<R>((s[0].d - s[1].d) * (hl + hr) / (hl * hl + hr * hr));
@@ -792,6 +847,7 @@ __host__ __device__ inline void edge_unit(const Dev &d, const Par &p, int e, int
     out[3 * k + 1] = src[k][1] * n0 - src[k][2] * n1;
     out[3 * k + 2] = src[k][1] * n1 + src[k][2] * n0;
   }
+  return true;
 }
 
 // ------------------------------------------------------------- cell unit
