@@ -60,7 +60,7 @@ N_SQ = 1024
 # edge_fused.
 WORK_PER_UNIT = {
     "fp32": {"recon": (2196, 0, 1069), "gate": (257, 0, 51), "iface": (836, 0, 265), "edge": (5405, 0, 374),
-             "edge_fused": (5723, 0, 350), "update": (298, 61, 570)},
+             "edge_fused": (5723, 0, 350), "update": (298, 61, 564)},
     "fp64": {"recon": (69, 4593, 2209), "gate": (280, 0, 63), "iface": (15, 1349, 473), "edge": (107, 9162, 696),
              "update": (0, 343, 850)},
 }

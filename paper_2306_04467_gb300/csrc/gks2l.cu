@@ -261,6 +261,25 @@ __global__ void k_harvest(Dev d, const int *perm, float tol, const float *logit_
 // per block, and for one of them a register budget of eight resident blocks
 // per SM); the autotuner (gks2l_autotune) picks one per kernel. The bodies
 // are shared; the entry points differ in their launch bounds only.
+// An edge's results for layer ell: the Gauss point q = 0 thread holds the
+// averaged F and F_t, the q = 1 thread W and W_t (avg[0..2], avg[3..5]). The
+// depth components of F and F_t also go out in FP64 for the cells' mass sums.
+template <typename R>
+__device__ __forceinline__ void edge_write(const Dev &d, int e, int ell, int q, int stage, const R avg[6]) {
+  const int NE = d.ne;
+  const int vb = ell == 0 ? 3 : 0;
+  R *A = (R *)(q == 0 ? d.eF : (stage == 1 ? d.eWn : d.eW));
+  R *B = (R *)(q == 0 ? d.eFt : d.eWt);
+  for (int k = 0; k < 3; k++) {
+    A[(vb + k) * NE + e] = avg[k];
+    B[(vb + k) * NE + e] = avg[3 + k];
+  }
+  if (q == 0) {
+    d.eFm[(vb / 3) * NE + e] = (double)avg[0];
+    d.eFtm[(vb / 3) * NE + e] = (double)avg[3];
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ void iface_body(const Dev &d) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -289,14 +308,7 @@ __device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage)
     avg[k] = (R)0.5 * (mine + __shfl_xor_sync(FULL, theirs, 1));
   }
   if (!ok) return;
-  const int NE = d.ne;
-  const int vb = ell == 0 ? 3 : 0;
-  R *A = (R *)(q == 0 ? d.eF : (stage == 1 ? d.eWn : d.eW));
-  R *B = (R *)(q == 0 ? d.eFt : d.eWt);
-  for (int k = 0; k < 3; k++) {
-    A[(vb + k) * NE + e] = avg[k];
-    B[(vb + k) * NE + e] = avg[3 + k];
-  }
+  edge_write<R>(d, e, ell, q, stage, avg);
 }
 
 // Gated runs: the interface levels and the edge solution in one kernel. Each
@@ -339,13 +351,7 @@ __device__ __forceinline__ void edge_fused_body(const Dev &d, const Par &p, int 
   const int NE = d.ne;
   if (q == 0) ((R *)d.hc)[ell * NE + e] = hcv;
   if (!done) return;
-  const int vb = ell == 0 ? 3 : 0;
-  R *A = (R *)(q == 0 ? d.eF : (stage == 1 ? d.eWn : d.eW));
-  R *B = (R *)(q == 0 ? d.eFt : d.eWt);
-  for (int k = 0; k < 3; k++) {
-    A[(vb + k) * NE + e] = avg[k];
-    B[(vb + k) * NE + e] = avg[3 + k];
-  }
+  edge_write<R>(d, e, ell, q, stage, avg);
 }
 
 // The worklist's units with the plane gradients (every blended level is
@@ -357,7 +363,6 @@ __global__ void __launch_bounds__(128) k_edge_deferred(Dev d, Par p, int stage) 
   const int n = *d.wl_count;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarp = (gridDim.x * blockDim.x) >> 5;
-  const int NE = d.ne;
   for (int base = warp * 16; base < n; base += nwarp * 16) {
     const int i = base + (lane >> 1), q = lane & 1;
     const int item = d.wl[i < n ? i : n - 1];
@@ -371,13 +376,7 @@ __global__ void __launch_bounds__(128) k_edge_deferred(Dev d, Par p, int stage) 
       avg[k] = (R)0.5 * (mine + __shfl_xor_sync(FULL, theirs, 1));
     }
     if (i >= n) continue;
-    const int vb = ell == 0 ? 3 : 0;
-    R *A = (R *)(q == 0 ? d.eF : (stage == 1 ? d.eWn : d.eW));
-    R *B = (R *)(q == 0 ? d.eFt : d.eWt);
-    for (int k = 0; k < 3; k++) {
-      A[(vb + k) * NE + e] = avg[k];
-      B[(vb + k) * NE + e] = avg[3 + k];
-    }
+    edge_write<R>(d, e, ell, q, stage, avg);
   }
 }
 
@@ -453,8 +452,10 @@ template <typename R, int BS>
 __global__ void __launch_bounds__(BS) k_iface(Dev d) { iface_body<R>(d); }
 template <typename R, int BS>
 __global__ void __launch_bounds__(BS) k_edge(Dev d, Par p, int stage) { edge_body<R>(d, p, stage); }
+// (the fused kernel's default shapes are held to 768 resident threads per SM,
+// the 80 registers its body compiles to when left alone)
 template <typename R, int BS>
-__global__ void __launch_bounds__(BS) k_edgef(Dev d, Par p, int stage) { edge_fused_body<R>(d, p, stage); }
+__global__ void __launch_bounds__(BS, 768 / BS) k_edgef(Dev d, Par p, int stage) { edge_fused_body<R>(d, p, stage); }
 template <typename R, int BS>
 __global__ void __launch_bounds__(BS) k_update(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
 template <typename R>
@@ -669,6 +670,7 @@ size_t layout(gks2l_ctx *c, char *base) {
   d.plane = k.take<char>(rs * 6 * cs);
   d.cedge = k.take<int>(3 * cs);
   d.fsl = k.take<double>(3 * cs);
+  d.fslR = k.take<char>(rs * 3 * cs);
   d.inst_first = k.take<int>(ni + 1);
   d.avg = k.take<double>(6 * cs);
   d.dq = k.take<char>(rs * 6 * cs);
@@ -677,6 +679,7 @@ size_t layout(gks2l_ctx *c, char *base) {
   d.Wn = k.take<double>(6 * cs);
   d.Ln = k.take<double>(6 * cs);
   d.Ltn = k.take<double>(6 * cs);
+  d.incR = k.take<char>(rs * 4 * cs);
   d.srec = k.take<char>(rs * 2 * NREC * cs);
   d.omg = k.take<char>(rs * 2 * cs);
   d.mlp = k.take<MlpDev>(1);
@@ -696,6 +699,8 @@ size_t layout(gks2l_ctx *c, char *base) {
   d.wl_count = k.take<int>(1);
   d.eF = k.take<char>(rs * 6 * ne);
   d.eFt = k.take<char>(rs * 6 * ne);
+  d.eFm = k.take<double>(2 * ne);
+  d.eFtm = k.take<double>(2 * ne);
   d.eW = k.take<char>(rs * 6 * ne);
   d.eWt = k.take<char>(rs * 6 * ne);
   d.eWn = k.take<char>(rs * 6 * ne);
@@ -1091,6 +1096,7 @@ int gks2l_bind(gks2l_ctx *c, void *d_workspace, size_t bytes, void *stream) {
       (rc = upload_rows<int>(c, c->d.st_cell, P.st_cell, kSlots)) ||
       (rc = upload_rows<int8_t>(c, c->d.st_xf, P.st_xf, kSlots)) ||
       (rc = upload_rows<int>(c, c->d.cedge, P.cedge, 3)) || (rc = upload_rows<double>(c, c->d.fsl, fsl, 3)) ||
+      (rc = upload_form(c, c->d.fslR, fsl, 3, true)) ||
       (rc = upload(c, c->d.inst_first, P.inst_first)) || (rc = upload(c, c->d.eL, P.eL)) ||
       (rc = upload(c, c->d.eR, P.eR)) || (rc = upload(c, c->d.exf, P.exf)) || (rc = upload(c, c->d.xf, xf)) ||
       (rc = upload(c, c->d_perm, P.perm)) ||

@@ -64,11 +64,13 @@ struct Dev {
   const void *plane;        // [(f*2+d)][cell] plane operator, type R
   const int *cedge;         // [f][cell]: edge id, or ~edge when the cell is the R side
   const double *fsl;        // [f][cell]: sign * |Gamma| / |Omega| (double, mass sums)
+  const void *fslR;         // the same, type R (the other residuals)
   const int *inst_first;
   double *avg;              // state averages [v][cell] (FP64)
   void *dq, *dg;            // deviation mirrors [6][cell], gradients [12][cell], type R
   void *hrefc;              // R1 - B_j per cell, type R
-  double *Wn, *Ln, *Ltn;    // stage snapshot (FP64)
+  double *Wn, *Ln, *Ltn;    // stage snapshot (FP64; L and L_t rows of the layer depths only)
+  void *incR;               // [4][cell] stage-1 part of the stage-2 momentum increment, type R
   void *srec;               // side records [layer][cell][NREC], type R (lower layer first)
   void *omg;                // omega_H / gamma_H of eta1 [0] and h2 [1], type R
   const void *mlp;          // gate network, packed image (MlpDev)
@@ -86,6 +88,8 @@ struct Dev {
   int *wl;                  // [2 * edge] (edge << 1 | layer) units left to the deferred edge pass
   int *wl_count;            // their number (zeroed before each fused edge launch)
   void *eF, *eFt, *eW, *eWt, *eWn;  // [6][edge] Gauss-point sums (weights 1/2), deviations, type R
+  double *eFm, *eFtm;       // [2][edge] the depth components of F, F_t (h2 first, then eta1) in
+                            // FP64, converted once per edge for the cells' FP64 mass sums
   // per instance
   double *ref;              // [inst*2]: R2, R1
   void *refR;               // the same, type R
@@ -875,17 +879,16 @@ __host__ __device__ inline double update_unit(const Dev &d, const Par &p, int j,
     int ce = d.cedge[f * N + j];
     int e = ce >= 0 ? ce : ~ce;
     const double sl = d.fsl[f * N + j];
-    const R slR = (R)sl;
+    const R slR = ((const R *)d.fslR)[f * N + j];
     const R nx = en[e], ny = en[NE + e];
     for (int v = 0; v < NV; v++) {
-      R F = eF[v * NE + e], Ft = eFt[v * NE + e];
       R W = Wcur[v * NE + e], Wt = eWt[v * NE + e], Wn = eWn[v * NE + e];
       if (v == 0 || v == 3) {
-        LFm[v / 3] -= sl * (double)F;
-        LFtm[v / 3] -= sl * (double)Ft;
+        LFm[v / 3] -= sl * d.eFm[(v / 3) * NE + e];
+        LFtm[v / 3] -= sl * d.eFtm[(v / 3) * NE + e];
       } else {
-        LF[v] -= slR * F;
-        LFt[v] -= slR * Ft;
+        LF[v] -= slR * eF[v * NE + e];
+        LFt[v] -= slR * eFt[v * NE + e];
       }
       mW[v] += W * (R)(1.0 / 3.0);
       mWt[v] += Wt * (R)(1.0 / 3.0);
@@ -912,24 +915,40 @@ __host__ __device__ inline double update_unit(const Dev &d, const Par &p, int j,
     L[4 + k] = LF[4 + k] - G * dq[3 * N + j] * gb[k] - chi * G * m1 * GG[0][k];
     Lt[4 + k] = LFt[4 + k] - G * LFh1 * gb[k] - chi * G * (mWt[3] * GG[0][k] + m1 * GGt[0][k]);
   }
-  double Ld[NV], Ltd[NV];
-  Ld[0] = LFm[0]; Ltd[0] = LFtm[0];
-  Ld[3] = LFm[1]; Ltd[3] = LFtm[1];
+  // S2O4 (Eq. SWE-fully-discrete): stage 1 W* = W^n + dt/2 L^n + dt^2/8 L_t^n;
+  // stage 2 W^{n+1} = W^n + dt L^n + dt^2/6 L_t^n + dt^2/3 L_t^*. The layer
+  // depths (exact conservation) in FP64 throughout; the momenta's increments
+  // in R (their residuals are R), each added to the FP64 state once
   const int mom[4] = {1, 2, 4, 5};
-  for (int i = 0; i < 4; i++) { Ld[mom[i]] = (double)L[mom[i]]; Ltd[mom[i]] = (double)Lt[mom[i]]; }
   double nw[NV];
-  for (int v = 0; v < NV; v++) {
-    double a = d.avg[v * N + j];
+  for (int m = 0; m < 2; m++) {
+    const int v = 3 * m;
+    const double a = d.avg[v * N + j];
     if (stage == 1) {
       if (act) {
         d.Wn[v * N + j] = a;
-        d.Ln[v * N + j] = Ld[v];
-        d.Ltn[v * N + j] = Ltd[v];
+        d.Ln[v * N + j] = LFm[m];
+        d.Ltn[v * N + j] = LFtm[m];
       }
-      nw[v] = a + 0.5 * dt * Ld[v] + 0.125 * dt * dt * Ltd[v];
+      nw[v] = a + 0.5 * dt * LFm[m] + 0.125 * dt * dt * LFtm[m];
     } else {
       nw[v] = d.Wn[v * N + j] + dt * d.Ln[v * N + j] + dt * dt * (1.0 / 6.0) * d.Ltn[v * N + j] +
-              dt * dt * (1.0 / 3.0) * Ltd[v];
+              dt * dt * (1.0 / 3.0) * LFtm[m];
+    }
+  }
+  R *inc = (R *)d.incR;
+  const R dt2 = dtr * dtr;
+  for (int i = 0; i < 4; i++) {
+    const int v = mom[i];
+    const double a = d.avg[v * N + j];
+    if (stage == 1) {
+      if (act) {
+        d.Wn[v * N + j] = a;
+        inc[i * N + j] = dtr * L[v] + dt2 * (R)(1.0 / 6.0) * Lt[v];
+      }
+      nw[v] = a + (double)((R)0.5 * dtr * L[v] + (R)0.125 * dt2 * Lt[v]);
+    } else {
+      nw[v] = d.Wn[v * N + j] + (double)(inc[i * N + j] + dt2 * (R)(1.0 / 3.0) * Lt[v]);
     }
   }
   if (act) {
