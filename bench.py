@@ -54,13 +54,14 @@ N_SQ = 1024
 # the same plus plane rows and blend weights, 24 interface values out;
 # edge_fused (the gated runs' interface levels and edge solution in one
 # kernel): the edge kernel's bytes without the plane rows, which the gate
-# makes unnecessary on this workload, plus the two levels out;
+# makes unnecessary on this workload, plus the two levels out and the depth
+# fluxes in FP64 in place of R;
 # update: three edges' fluxes and interface values, state in/out with the
 # S2O4 snapshot, mirrors out). Units: cells for recon, gate and update, edges for iface, edge and
 # edge_fused.
 WORK_PER_UNIT = {
     "fp32": {"recon": (2196, 0, 1069), "gate": (257, 0, 51), "iface": (836, 0, 265), "edge": (5405, 0, 374),
-             "edge_fused": (5723, 0, 350), "update": (298, 61, 564)},
+             "edge_fused": (5719, 0, 366), "update": (317, 45, 564)},
     "fp64": {"recon": (69, 4593, 2209), "gate": (280, 0, 63), "iface": (15, 1349, 473), "edge": (107, 9162, 696),
              "update": (0, 343, 850)},
 }
@@ -68,8 +69,8 @@ WORK_PER_UNIT = {
 PEAK_TFLOPS = {"fp32": 76.5, "fp64": 1.254}
 # DRAM bytes per unit (dram__bytes_read.sum + dram__bytes_write.sum of the
 # same launches, per unit; inputs larger than L2, traffic grows with units).
-TRAFFIC_PER_UNIT = {"fp32": {"recon": 1028.0, "gate": 51.0, "iface": 259.0, "edge": 327.0, "edge_fused": 333.0,
-                             "update": 455.0}}
+TRAFFIC_PER_UNIT = {"fp32": {"recon": 1027.0, "gate": 51.0, "iface": 259.0, "edge": 327.0, "edge_fused": 359.0,
+                             "update": 445.0}}
 
 
 KERNEL_NAME = {"edge_fused": "k_edgef", "edge_deferred": "k_edge_deferred"}
