@@ -32,6 +32,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr unsigned long long DBL_INF_BITS = 0x7FF0000000000000ull;
 constexpr int TW = 32;                  // cells per reconstruction tile
+constexpr int REF_CHUNK = 4096;         // cells per chunk of the reference-level reduction
 constexpr int ST_TIMEOUT = 4;           // status bit: a bounded wait gave up
 constexpr int GATE_LD = 40;             // padded row stride of the gate feature tile (bank spread)
 
@@ -498,6 +499,50 @@ __global__ void __launch_bounds__(128) k_cfl(Dev d, Par p) {
   reduce_cfl(d, ok, inst, ratio);
 }
 
+// Reference levels of each instance (R2, R1): the area-weighted means of h2
+// and eta1 = h1 + B, rounded to 2^-32. Deterministic: fixed chunks of an
+// instance's cells, each summed in a fixed order (thread-strided, then a
+// shared-memory tree), then the chunks in order by one thread per instance.
+constexpr int REF_THREADS = 256;
+__global__ void __launch_bounds__(REF_THREADS) k_ref_partial(Dev d, const int *chunk, double *part) {
+  __shared__ double sh[3][REF_THREADS];
+  const int c = blockIdx.x, t = threadIdx.x, j1 = chunk[2 * c + 1];
+  double a = 0, s2 = 0, s1 = 0;
+  for (int j = chunk[2 * c] + t; j < j1; j += REF_THREADS) {
+    const double w = d.area[j];
+    a += w;
+    s2 += w * d.avg[j];
+    s1 += w * (d.avg[3 * d.cs + j] + d.bmean[j]);
+  }
+  sh[0][t] = a;
+  sh[1][t] = s2;
+  sh[2][t] = s1;
+  __syncthreads();
+  for (int o = REF_THREADS / 2; o > 0; o >>= 1) {
+    if (t < o)
+      for (int k = 0; k < 3; k++) sh[k][t] += sh[k][t + o];
+    __syncthreads();
+  }
+  if (t < 3) part[3 * c + t] = sh[t][0];
+}
+
+template <typename R>
+__global__ void k_ref_final(Dev d, const int *inst_chunk, const double *part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.ninst) return;
+  double a = 0, s2 = 0, s1 = 0;
+  for (int c = inst_chunk[i]; c < inst_chunk[i + 1]; c++) {
+    a += part[3 * c];
+    s2 += part[3 * c + 1];
+    s1 += part[3 * c + 2];
+  }
+  const double r2 = ldexp(rint(ldexp(s2 / a, 32)), -32), r1 = ldexp(rint(ldexp(s1 / a, 32)), -32);
+  d.ref[2 * i] = r2;
+  d.ref[2 * i + 1] = r1;
+  ((R *)d.refR)[2 * i] = (R)r2;
+  ((R *)d.refR)[2 * i + 1] = (R)r1;
+}
+
 __global__ void k_reset_stats(Dev d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.ninst) return;
@@ -630,7 +675,10 @@ struct gks2l_ctx {
   int *d_perm = nullptr;
   double *d_tend = nullptr;
   double *d_stage = nullptr;   // 18 * nt staging for permutations
-  std::vector<double> bmean_h; // cell-average bottom (device order), host copy
+  int nchunk = 0;              // reference-level reduction: chunks of one instance's cells
+  int *d_chunk = nullptr;      // [nchunk][2] first and end cell of each chunk
+  int *d_inst_chunk = nullptr; // [ninst + 1] first chunk of each instance
+  double *d_refpart = nullptr; // [nchunk][3] the chunks' sums
   bool has_mlp = false;
   int n_sm = 1;                // SMs of the bound device
   cudaStream_t side = nullptr; // second stream for the gate (created with the network)
@@ -717,6 +765,12 @@ size_t layout(gks2l_ctx *c, char *base) {
   c->d_perm = k.take<int>(nt);
   c->d_tend = k.take<double>(1);
   c->d_stage = k.take<double>(18 * nt);
+  // at most one chunk per instance plus one per REF_CHUNK cells (the sizes
+  // only: the workspace size is asked for before the instances are known)
+  const size_t max_chunks = ni + nt / REF_CHUNK + 1;
+  c->d_chunk = k.take<int>(2 * max_chunks);
+  c->d_inst_chunk = k.take<int>(ni + 1);
+  c->d_refpart = k.take<double>(3 * max_chunks);
   return k.off + 256;
 }
 
@@ -794,7 +848,6 @@ inline unsigned blocks(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b
 int upload_bathymetry(gks2l_ctx *c) {
   std::vector<double> bm, bx, by, e0, e1;
   bathymetry(c->prep, c->has_b ? c->bvert.data() : nullptr, bm, bx, by, e0, e1);
-  c->bmean_h = bm;
   std::vector<double> bg(2 * (size_t)c->prep.nt);
   std::copy(bx.begin(), bx.end(), bg.begin());
   std::copy(by.begin(), by.end(), bg.begin() + c->prep.nt);
@@ -952,40 +1005,19 @@ int check_status(gks2l_ctx *c) {
 
 // Reference levels per instance: area-weighted means of h2 and eta1 = h1 + B
 // of the state in device order (host, deterministic), rounded to 2^-32.
-int set_references(gks2l_ctx *c, const double *avg_dev_order_host) {
-  const Prep &P = c->prep;
-  const size_t N = c->cs;
-  std::vector<double> ref(2 * P.ninst);
-  for (int i = 0; i < P.ninst; i++) {
-    double a = 0, s2 = 0, s1 = 0;
-    for (int j = P.inst_first[i]; j < P.inst_first[i + 1]; j++) {
-      a += P.area[j];
-      s2 += P.area[j] * avg_dev_order_host[j];
-      s1 += P.area[j] * (avg_dev_order_host[3 * N + j] + c->bmean_h[j]);
-    }
-    ref[2 * i] = std::ldexp(std::nearbyint(std::ldexp(s2 / a, 32)), -32);
-    ref[2 * i + 1] = std::ldexp(std::nearbyint(std::ldexp(s1 / a, 32)), -32);
-  }
-  int rc;
-  if ((rc = upload(c, c->d.ref, ref)) || (rc = upload_form(c, c->d.refR, ref, 1, false))) return rc;
-  return 0;
-}
-
 // after d.avg (device order) is set and the caller's gradients sit at
 // grad_caller (device memory, caller order, or NULL): references, mirrors,
 // reference depths on the edges, counters, CFL ratio and masses
 int after_state(gks2l_ctx *c, const double *grad_caller) {
-  const size_t N = c->cs;
-  std::vector<double> avg(6 * N);
-  CK(cudaMemcpyAsync(avg.data(), c->d.avg, 6 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  int rc = set_references(c, avg.data());
-  if (rc) return rc;
+  // the reference levels on the device (no copy of the state to the host)
+  k_ref_partial<<<c->nchunk, REF_THREADS, 0, c->stream>>>(c->d, c->d_chunk, c->d_refpart);
   Par p = make_par(c);
   if (c->par.precision == GKS2L_FP32) {
+    k_ref_final<float><<<blocks(c->d.ninst, 128), 128, 0, c->stream>>>(c->d, c->d_inst_chunk, c->d_refpart);
     k_mirrors<float><<<blocks(c->d.nt, 128), 128, 0, c->stream>>>(c->d, c->d_perm, grad_caller);
     k_edge_ref<float><<<blocks(c->d.ne, 128), 128, 0, c->stream>>>(c->d);
   } else {
+    k_ref_final<double><<<blocks(c->d.ninst, 128), 128, 0, c->stream>>>(c->d, c->d_inst_chunk, c->d_refpart);
     k_mirrors<double><<<blocks(c->d.nt, 128), 128, 0, c->stream>>>(c->d, c->d_perm, grad_caller);
     k_edge_ref<double><<<blocks(c->d.ne, 128), 128, 0, c->stream>>>(c->d);
   }
@@ -1106,6 +1138,27 @@ int gks2l_bind(gks2l_ctx *c, void *d_workspace, size_t bytes, void *stream) {
       (rc = upload_form(c, c->d.epsA, epsA, 1, false)) || (rc = upload_form(c, c->d.exiL, P.exiL, 1, false)) ||
       (rc = upload_form(c, c->d.exiR, P.exiR, 1, false)) || (rc = upload_form(c, c->d.en, en, 1, false)))
     return rc;
+  {
+    std::vector<int> ch, ich(P.ninst + 1);
+    for (int i = 0; i < P.ninst; i++) {
+      ich[i] = (int)(ch.size() / 2);
+      const int j0 = P.inst_first[i], j1 = P.inst_first[i + 1];
+      int j = j0;
+      do {
+        const int e = std::min(j1, j + REF_CHUNK);
+        ch.push_back(j);
+        ch.push_back(e);
+        j = e;
+      } while (j < j1);
+    }
+    ich[P.ninst] = (int)(ch.size() / 2);
+    c->nchunk = (int)(ch.size() / 2);
+    if ((size_t)c->nchunk > (size_t)P.ninst + (size_t)P.nt / REF_CHUNK + 1) {
+      c->err = "reference chunk table larger than its slice";
+      return GKS2L_EINVAL;
+    }
+    if ((rc = upload(c, c->d_chunk, ch)) || (rc = upload(c, c->d_inst_chunk, ich))) return rc;
+  }
   {
     int dev = 0;
     CK(cudaGetDevice(&dev));
