@@ -18,10 +18,12 @@
  * Parity notes: every routine here is pinned by a CPU test (moments and time
  * integrals against quadrature, the point solution against brute-force
  * velocity/time quadrature, cubic reproduction, Gauss-theorem exactness,
- * uniform flux, lake at rest, conservation, convergence order). The WENO
- * constants (R5), the edge weight w (R6) and the literal xi argument (R7) are
- * not fixed by the paper: for them parity is unpinned against the paper and
- * fixed only by the readings and the invariants above.
+ * uniform flux, lake at rest, conservation, convergence order). The blend
+ * of Sec. 2.3 is pinned in its closed-form cases (xi = 1/2 at rest, xi = 0
+ * or 1 in strong flow, against the two sides' point values). The WENO
+ * constants (R5) and the edge weight w (R6) are not fixed by the paper: for
+ * them parity is unpinned against the paper and fixed only by the readings
+ * and the invariants above.
  */
 #include <math.h>
 #include <stdio.h>
@@ -1368,6 +1370,12 @@ void orc_gauss_gradient(const orc_t *o, const double *pv /* ne*2 */, double *g /
     g[2 * j] = s[0] / o->area[j];
     g[2 * j + 1] = s[1] / o->area[j];
   }
+}
+/* edge-centre blended levels of the last stage (Sec. 2.3), formed from the  */
+/* stage-start reconstruction: per edge, the lower layer's depth h1-hat and  */
+/* the upper layer's h2-hat                                                  */
+void orc_blend_levels(const orc_t *o, double *hc /* ne*2 */) {
+  memcpy(hc, o->hc, sizeof(double) * 2 * (size_t)o->ne);
 }
 /* interface data of the last stage: per edge per Gauss point, 6 values each */
 void orc_edge_outputs(const orc_t *o, double *F, double *Ft, double *W, double *Wt) {

@@ -65,6 +65,7 @@ def lib():
         _lib.orc_gate_features.argtypes = [p, p]
         _lib.orc_stencil_size.argtypes = [p, i]
         _lib.orc_edge_points.argtypes = [p, p, p]
+        _lib.orc_blend_levels.argtypes = [p, p]
         _lib.orc_gauss_gradient.argtypes = [p, p, p]
         _lib.orc_edge_outputs.argtypes = [p, p, p, p, p]
         _lib.orc_raw_moments.argtypes = [d, d, i, i, p]
@@ -193,6 +194,13 @@ class Oracle:
         lr = np.zeros((self.ne, 2), dtype=np.int32)
         lib().orc_edge_points(self._h, _ptr(xq), _ptr(lr))
         return xq, lr
+
+    def blend_levels(self):
+        """Edge-centre blended levels of the last stage (Sec. 2.3): [ne, 2] =
+        (lower-layer depth h1-hat, upper-layer h2-hat)."""
+        hc = np.zeros(2 * self.ne)
+        lib().orc_blend_levels(self._h, _ptr(hc))
+        return hc.reshape(self.ne, 2)
 
     def gauss_gradient(self, point_values):
         pv = np.ascontiguousarray(point_values, dtype=np.float64).reshape(self.ne, 2)

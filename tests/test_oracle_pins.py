@@ -384,3 +384,67 @@ def test_rest_state_noise_does_not_grow_at_small_cfl():
     o.advance(600)
     a, _ = o.get_state()
     assert np.abs(a[3] - 0.7).max() <= 3e-8
+
+
+def _blend_case(velocity):
+    """A periodic jittered mesh with smooth, non-constant levels and a uniform
+    velocity: the oracle's blended levels of one stage and the two sides'
+    reconstructions evaluated at the Gauss points of every edge that does
+    not cross the periodic seam (there the neighbour is a translated image)."""
+    mesh = inputs.jittered_mesh(10, 10, seed=5, bc="periodic")
+    tp = 2 * math.pi
+    f1 = lambda x, y: 0.6 + 0.05 * np.sin(tp * x) * np.cos(tp * y)
+    f2 = lambda x, y: 0.4 + 0.03 * np.cos(tp * x)
+    avg = np.zeros((6, mesh.n_tri))
+    avg[3] = inputs.cell_average(f1, mesh, 5)
+    avg[0] = inputs.cell_average(f2, mesh, 5)
+    for b in (0, 3):
+        avg[b + 1] = velocity[0] * avg[b]
+        avg[b + 2] = velocity[1] * avg[b]
+    o = orc.Oracle(mesh, None, g=G, chi=0.5)
+    o.set_state(avg, np.zeros((6, 2, mesh.n_tri)))
+    o.reconstruct()
+    xq, lr = o.edge_points()
+    _, cx, cy = o.geometry()
+    inner = [e for e in range(o.ne)
+             if np.hypot(cx[lr[e, 1]] - cx[lr[e, 0]], cy[lr[e, 1]] - cy[lr[e, 0]]) < 0.3]
+    sides = {}
+    for e in inner:
+        sides[e] = [(o.eval(lr[e, 0], *xq[e, q])[0], o.eval(lr[e, 1], *xq[e, q])[0]) for q in range(2)]
+    o.advance(1)
+    return o.blend_levels(), xq, lr, cx, cy, sides
+
+
+def test_blended_levels_at_rest_are_the_mean_of_both_sides():
+    """Sec. 2.3: h-hat = xi h^l + (1 - xi) h^r with xi = erfc((U^l + U^r)/2)/2;
+    at rest erfc(0) = 1 gives xi = 1/2, so the edge-centre level is the mean,
+    over the two Gauss points, of the two cells' reconstructed values (here
+    from the oracle's own point evaluation, flat bottom so depth = level)."""
+    hc, _, _, _, _, sides = _blend_case((0.0, 0.0))
+    for e, pts in sides.items():
+        want1 = np.mean([0.5 * (l[3] + r[3]) for l, r in pts])
+        want2 = np.mean([0.5 * (l[0] + r[0]) for l, r in pts])
+        assert abs(hc[e, 0] - want1) <= 1e-15 and abs(hc[e, 1] - want2) <= 1e-15, e
+
+
+def test_blended_levels_in_strong_flow_take_one_side():
+    """The limits of the same blend: with a normal velocity of 30 or more
+    (uniform flow of 60 along x, edges whose normal from L to R has
+    |n_x| > 1/2) erfc is 0 or 2 to double precision, so the level is the
+    R cell's value where U_n > 0 and the L cell's where U_n < 0 (the sign as
+    the paper prints it)."""
+    hc, xq, lr, cx, cy, sides = _blend_case((60.0, 0.0))
+    checked = 0
+    for e, pts in sides.items():
+        t = xq[e, 1] - xq[e, 0]
+        n = np.array([t[1], -t[0]]) / np.hypot(*t)
+        if n @ np.array([cx[lr[e, 1]] - cx[lr[e, 0]], cy[lr[e, 1]] - cy[lr[e, 0]]]) < 0:
+            n = -n
+        if abs(n[0]) <= 0.5:
+            continue
+        k = 1 if n[0] > 0 else 0          # R side downstream of the flow, else L
+        want1 = np.mean([p[k][3] for p in pts])
+        want2 = np.mean([p[k][0] for p in pts])
+        assert abs(hc[e, 0] - want1) <= 1e-15 and abs(hc[e, 1] - want2) <= 1e-15, e
+        checked += 1
+    assert checked > 50
