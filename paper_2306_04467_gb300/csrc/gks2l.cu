@@ -1,15 +1,18 @@
 // gks2l: CUDA kernels (sm_103a) and the C ABI of include/gks2l.h.
 //
-// One S2O4 stage (arXiv 2306.04467, Eq. SWE-fully-discrete) is four kernels
-// over structure-of-arrays data in a Morton-renumbered cell order:
+// One S2O4 stage (arXiv 2306.04467, Eq. SWE-fully-discrete) over
+// structure-of-arrays data in a Morton-renumbered cell order:
 //   k_recon   (32 cells x 6 variables per block) compact P3/WENO reconstruction
-//             (Sec. 3.4); the block's operator rows are staged into shared
-//             memory by TMA (cp.async.bulk.tensor) behind an mbarrier
+//             (Sec. 3.4); the tile's operator rows arrive in shared memory by
+//             bulk copy (cp.async.bulk) behind an mbarrier
 //   k_iface   (edge x layer)         blended interface levels h-hat (Sec. 2.3)
 //   k_edge    (edge x layer x point) gas-kinetic interface solution (Eq. SWE-2nd-order)
 //   k_update  (cell)                 fluxes, sources, S2O4 update, Gauss-theorem
 //                                    gradients (Eqs. SWE-semi-flux, slope-1, S2O3),
-//                                    CFL and conservation reductions
+//                                    CFL reduction
+// With the learned troubled-cell gate, k_gate (next stage's mask) runs on a
+// second stream, and k_iface + k_edge become k_edgef (both in one pass where
+// the plane gradients carry no weight) + k_edge_deferred (the other edges).
 // A step is k_step_begin + two stages, captured once into a CUDA graph.
 #include <cuda_runtime.h>
 
