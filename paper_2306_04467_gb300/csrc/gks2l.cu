@@ -261,10 +261,6 @@ __global__ void k_harvest(Dev d, const int *perm, float tol, const float *logit_
   if (logits) logits[c] = logit_dev[j];
 }
 
-// The interface, edge and update kernels come in four launch shapes (threads
-// per block, and for one of them a register budget of eight resident blocks
-// per SM); the autotuner (gks2l_autotune) picks one per kernel. The bodies
-// are shared; the entry points differ in their launch bounds only.
 // An edge's results for layer ell: the Gauss point q = 0 thread holds the
 // averaged F and F_t, the q = 1 thread W and W_t (avg[0..2], avg[3..5]). The
 // depth components of F and F_t also go out in FP64 for the cells' mass sums.
@@ -452,6 +448,10 @@ __device__ __forceinline__ void update_body(const Dev &d, const Par &p, int stag
   if (ok && j == d.inst_first[inst]) d.t[inst] += d.dt[inst];
 }
 
+// The interface, edge (fused edge) and update kernels come in five launch
+// shapes (threads per block, and for two of them a register budget); the
+// autotuner (gks2l_autotune) picks one per kernel. The bodies are shared;
+// the entry points differ in their launch bounds only.
 template <typename R, int BS>
 __global__ void __launch_bounds__(BS) k_iface(Dev d) { iface_body<R>(d); }
 template <typename R, int BS>
@@ -699,7 +699,7 @@ namespace {
 size_t layout(gks2l_ctx *c, char *base) {
   const Prep &P = c->prep;
   const size_t nt = P.nt, ne = P.ne, ni = P.ninst, rs = c->rsize;
-  const size_t cs = (nt + TW - 1) / TW * TW + TW;   // one spare tile keeps every TMA box in bounds
+  const size_t cs = (nt + TW - 1) / TW * TW + TW;   // one spare tile past the last one read
   c->cs = (int)cs;
   Carver k{base};
   Dev &d = c->d;
