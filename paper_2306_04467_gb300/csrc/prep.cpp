@@ -333,6 +333,15 @@ int prepare(int n, const gks2l_mesh *meshes, Prep &out, std::string &err) {
       const PE &q = pes[found];
       int c1 = p.h / 3, k1 = p.h % 3, c2 = q.h / 3, k2 = q.h % 3;
       double sx = p.mx - q.mx, sy = p.my - q.my;  // maps c2's frame into c1's
+      // the partner must be the same edge translated (end points swapped:
+      // both triangles are counter-clockwise, on opposite sides)
+      const double *a0 = cells[c1].p[k1], *a1 = cells[c1].p[(k1 + 1) % 3];
+      const double *b0 = cells[c2].p[k2], *b1 = cells[c2].p[(k2 + 1) % 3];
+      if (std::fabs(b0[0] + sx - a1[0]) > tol || std::fabs(b0[1] + sy - a1[1]) > tol ||
+          std::fabs(b1[0] + sx - a0[0]) > tol || std::fabs(b1[1] + sy - a0[1]) > tol) {
+        err = "periodic sides do not match";
+        return GKS2L_EMESH;
+      }
       face[p.h].nb = c2; face[p.h].nbk = k2; face[p.h].T = iso_shift(sx, sy);
       face[q.h].nb = c1; face[q.h].nbk = k1; face[q.h].T = iso_shift(-sx, -sy);
     }

@@ -66,3 +66,48 @@ def test_workspace_size_is_known_on_the_host():
             lib.gks2l_destroy(h)
     for n in (1, 3):
         assert sizes[gks2l.GKS2L_FP32, n] < sizes[gks2l.GKS2L_FP64, n]
+
+
+def _create(xy, tri, bc=None, period=(0.0, 0.0), **par):
+    """gks2l_create on host arrays (no GPU is touched); returns its code and
+    destroys a context it made."""
+    import ctypes
+    import numpy as np
+    lib = gks2l.load()
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    bcp = None
+    if bc is not None:
+        bc = np.ascontiguousarray(bc, dtype=np.int8)
+        bcp = bc.ctypes.data_as(gks2l._P)
+    m = gks2l.gks2l_mesh(len(xy), xy.ctypes.data_as(gks2l._P), len(tri), tri.ctypes.data_as(gks2l._P), bcp,
+                         (ctypes.c_double * 2)(*period))
+    p = gks2l.default_params(**par)
+    h = gks2l._P()
+    rc = lib.gks2l_create(ctypes.byref(m), ctypes.byref(p), ctypes.byref(h))
+    if rc == 0:
+        lib.gks2l_destroy(h)
+    return rc
+
+
+def test_create_rejects_unusable_input_on_the_host():
+    """Bad meshes and parameters come back as error codes from gks2l_create
+    (never a crash): an empty mesh or a bad parameter is EINVAL; a vertex
+    index out of range, a clockwise triangle, a periodic side without a
+    partner or one whose partner is not its translate is EMESH. A square of
+    two triangles with walls, or periodic with period 1, is accepted."""
+    import numpy as np
+    EINVAL, EMESH = -1, -2
+    sq = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+    ok = np.array([[0, 1, 2], [0, 2, 3]])
+    assert _create(sq, ok) == 0
+    assert _create(sq, ok[:0]) == EINVAL
+    assert _create(sq, np.array([[0, 1, 7], [0, 2, 3]])) == EMESH
+    assert _create(sq, np.array([[0, 2, 1], [0, 2, 3]])) == EMESH
+    periodic = np.full((2, 3), 2, dtype=np.int8)
+    assert _create(sq, ok, bc=periodic, period=(1.0, 1.0)) == 0
+    assert _create(sq, ok, bc=periodic, period=(2.0, 2.0)) == EMESH      # no partners
+    assert _create(sq, ok, bc=periodic, period=(0.5, 0.5)) == EMESH      # partners not translates
+    for bad in (dict(g=0.0), dict(cfl=-1.0), dict(eps=0.0), dict(chi=0.0), dict(weno_gamma_hi=1.5),
+                dict(precision=7)):
+        assert _create(sq, ok, **bad) == EINVAL, bad
