@@ -139,9 +139,15 @@ int gks2l_bind(gks2l_ctx *ctx, void *d_workspace, size_t bytes, void *stream);
 int gks2l_set_bathymetry(gks2l_ctx *ctx, const double *b_vert);
 
 /* Set the state from host arrays (avg: 6*n_tri, grad: 12*n_tri or NULL for
- * zero gradients) in the caller's order; resets time and step counters. */
+ * zero gradients) in the caller's order; resets time and step counters.
+ * Each instance's reference levels (the area-weighted means of h2 and
+ * h1 + B, rounded to 2^-32, about which the FP32 form computes deviations)
+ * are reduced on the device in a fixed order. Returns after the host arrays
+ * have been read (synchronises the stream). */
 int gks2l_set_state(gks2l_ctx *ctx, const double *avg, const double *grad);
-/* Same from device arrays (caller order) on the bound stream. */
+/* Same from device arrays (caller order), enqueued on the bound stream
+ * without synchronising; the arrays must stay valid until the stream has
+ * run it. */
 int gks2l_set_state_device(gks2l_ctx *ctx, const double *d_avg, const double *d_grad);
 
 /* Advance by up to n_stages stages (two stages make one S2O4 step). With
