@@ -718,6 +718,10 @@ static void vp_extent(const vpoly_t *p, int *mi, int *mj) {
     for (int j = 0; j < PP; j++)
       if (p->c[i][j] != 0) { if (i > *mi) *mi = i; if (j > *mj) *mj = j; }
 }
+/* set when a product would exceed the polynomial degree the kernels have: */
+/* only non-finite coefficients (a non-physical interface state) do that;   */
+/* orc_advance then stops with an error code instead of going on            */
+static _Thread_local int vp_overflow = 0;
 static void vp_mul(const vpoly_t *a, const vpoly_t *b, vpoly_t *out) {
   vpoly_t r;
   int ai, aj, bi, bj;
@@ -729,7 +733,7 @@ static void vp_mul(const vpoly_t *a, const vpoly_t *b, vpoly_t *out) {
       if (a->c[i][j] == 0) continue;
       for (int k = 0; k <= bi; k++)
         for (int l = 0; l <= bj; l++) {
-          if (i + k >= PP || j + l >= PP) { fprintf(stderr, "oracle: kernel degree overflow\n"); abort(); }
+          if (i + k >= PP || j + l >= PP) { vp_overflow = 1; continue; }
           r.c[i + k][j + l] += a->c[i][j] * b->c[k][l];
         }
     }
@@ -1271,6 +1275,10 @@ int orc_advance(orc_t *o, int n_stages, double t_end, double *t_out) {
       o->phase = 0;
     }
     o->stages_done++;
+    if (vp_overflow) {
+      vp_overflow = 0;
+      return -11;   /* a non-finite interface state in this stage */
+    }
   }
   if (t_out) *t_out = o->t;
   return 0;

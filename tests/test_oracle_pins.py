@@ -448,3 +448,19 @@ def test_blended_levels_in_strong_flow_take_one_side():
         assert abs(hc[e, 0] - want1) <= 1e-15 and abs(hc[e, 1] - want2) <= 1e-15, e
         checked += 1
     assert checked > 50
+
+
+def test_non_physical_interface_state_is_an_error_not_a_crash():
+    """A uniform 60 m/s flow driven head-on into walls makes the mirrored
+    interface states non-physical within one stage; the oracle reports that
+    as an error (the host process survives) instead of stopping it."""
+    mesh = inputs.jittered_mesh(10, 10, seed=5, bc="wall")
+    avg = np.zeros((6, mesh.n_tri))
+    avg[3] = 0.6
+    avg[0] = 0.4
+    avg[4] = 60.0 * avg[3]
+    avg[1] = 60.0 * avg[0]
+    o = orc.Oracle(mesh, None, g=G, chi=0.5)
+    o.set_state(avg, np.zeros((6, 2, mesh.n_tri)))
+    with pytest.raises(RuntimeError):
+        o.advance(4)
