@@ -36,6 +36,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2306_04467_gb300 import replicas  # noqa: E402  (host helpers only; no GPU work at import)
+from paper_2306_04467_gb300.replicas import dist_env  # noqa: E402
+
 METRIC = "triangle-stage updates/s vs plain FP64 GPU at stated L1 error; % roofline"
 UNIT = "triangle-stage updates/s"
 N_SQ = 1024
@@ -155,13 +158,6 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
 def oracle_rate(seconds_budget=15.0, n=48, stages_per_step=2, max_steps=None):
     """The FP64 CPU oracle on a bounded sample of the same workload: the same
     problem on an n x n-square mesh; returns (triangle-stages/s, description)."""
@@ -273,11 +269,7 @@ def main():
             torch.distributed.barrier()
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return x if ws == 1 else replicas.max_over_ranks(x, dev)
 
     # CPU baseline first (host cores, before any GPU work): rank 0 only
     cpu = None
@@ -388,8 +380,8 @@ def main():
                 l1_smooth["smooth_fraction"] = s.stats()["smooth_fraction"]
 
     rh = results["fp32_learned"]
-    value = ws * nt * 2 / (rh["ms_per_step"] * 1e-3)
-    rates = {f: ws * nt * 2 / (results[f]["ms_per_step"] * 1e-3) for f in results}
+    value = replicas.job_rate(nt * 2, rh["ms_per_step"], ws)
+    rates = {f: replicas.job_rate(nt * 2, results[f]["ms_per_step"], ws) for f in results}
     # roofline of the dominant kernel of the headline form
     # with the gate the interface levels and the edge solution run as one fused
     # kernel (the library reports it in the edge slot) followed by a pass over
