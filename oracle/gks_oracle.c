@@ -1385,6 +1385,11 @@ void orc_gauss_gradient(const orc_t *o, const double *pv /* ne*2 */, double *g /
 void orc_blend_levels(const orc_t *o, double *hc /* ne*2 */) {
   memcpy(hc, o->hc, sizeof(double) * 2 * (size_t)o->ne);
 }
+/* per cell, the gradients of the planes through its three edge-centre      */
+/* blended levels of the last stage (Sec. 2.3): d/dx, d/dy of h1-hat, h2-hat */
+void orc_plane_gradients(const orc_t *o, double *pg /* nt*4 */) {
+  memcpy(pg, o->plane, sizeof(double) * 4 * (size_t)o->nt);
+}
 /* interface data of the last stage: per edge per Gauss point, 6 values each */
 void orc_edge_outputs(const orc_t *o, double *F, double *Ft, double *W, double *Wt) {
   size_t n = (size_t)o->ne * 2 * NVAR;

@@ -66,6 +66,7 @@ def lib():
         _lib.orc_stencil_size.argtypes = [p, i]
         _lib.orc_edge_points.argtypes = [p, p, p]
         _lib.orc_blend_levels.argtypes = [p, p]
+        _lib.orc_plane_gradients.argtypes = [p, p]
         _lib.orc_gauss_gradient.argtypes = [p, p, p]
         _lib.orc_edge_outputs.argtypes = [p, p, p, p, p]
         _lib.orc_raw_moments.argtypes = [d, d, i, i, p]
@@ -201,6 +202,14 @@ class Oracle:
         hc = np.zeros(2 * self.ne)
         lib().orc_blend_levels(self._h, _ptr(hc))
         return hc.reshape(self.ne, 2)
+
+    def plane_gradients(self):
+        """Per cell, the gradients of the planes through its three edge-centre
+        blended levels of the last stage (Sec. 2.3): [nt, 2, 2] = (h1-hat,
+        h2-hat) x (d/dx, d/dy)."""
+        pg = np.zeros(4 * self.nt)
+        lib().orc_plane_gradients(self._h, _ptr(pg))
+        return pg.reshape(self.nt, 2, 2)
 
     def gauss_gradient(self, point_values):
         pv = np.ascontiguousarray(point_values, dtype=np.float64).reshape(self.ne, 2)

@@ -464,3 +464,31 @@ def test_non_physical_interface_state_is_an_error_not_a_crash():
     o.set_state(avg, np.zeros((6, 2, mesh.n_tri)))
     with pytest.raises(RuntimeError):
         o.advance(4)
+
+
+def test_planes_through_blended_levels_are_exact_for_linear_levels():
+    """Sec. 2.3's per-cell plane through the three edge-centre blended levels:
+    for linear levels at rest the reconstruction is exact (it reproduces
+    cubics) and xi = 1/2 averages two equal values, so each edge's level is
+    the field at its midpoint and every plane carries the field's exact
+    gradient, in both layers. Checked on the cells whose stencils and
+    neighbours' stencils stay clear of the walls (a wall's mirror image of a
+    linear field is not its continuation)."""
+    mesh = inputs.jittered_mesh(16, 16, seed=11, bc="wall")
+    f1 = lambda x, y: 0.6 + 0.08 * x - 0.03 * y
+    f2 = lambda x, y: 0.4 + 0.02 * x + 0.05 * y
+    avg = np.zeros((6, mesh.n_tri))
+    grad = np.zeros((6, 2, mesh.n_tri))
+    avg[3] = inputs.cell_average(f1, mesh, 4)
+    avg[0] = inputs.cell_average(f2, mesh, 4)
+    grad[3, 0], grad[3, 1] = 0.08, -0.03
+    grad[0, 0], grad[0, 1] = 0.02, 0.05
+    o = orc.Oracle(mesh, None, g=G, chi=0.5)
+    o.set_state(avg, grad)
+    o.advance(1)
+    pg = o.plane_gradients()
+    _, cx, cy = o.geometry()
+    inner = np.minimum(np.minimum(cx, 1 - cx), np.minimum(cy, 1 - cy)) >= 0.2
+    assert inner.sum() >= 150
+    want = np.array([[0.08, -0.03], [0.02, 0.05]])
+    assert np.abs(pg[inner] - want[None]).max() < 1e-12
