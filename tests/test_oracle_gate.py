@@ -126,3 +126,25 @@ def test_gate_features_on_linear_data():
             raw[2::3] = hs * coef[v][2]
             ref = raw / np.sqrt(np.sum(raw ** 2) + orc.WENO_EPS * area[t] * (1 + q[0] ** 2))
             assert np.abs(X[t, 12 * s:12 * s + 12] - ref).max() <= 1e-13, (t, v)
+
+
+def test_p3_weight_collapses_at_a_jump_and_is_linear_away_from_it():
+    """The nonlinear reconstruction exists to handle discontinuities (Sec. 3.4)
+    and the edge weight w of Sec. 2.3 is its P3 weight over the linear one
+    (reading R6): on a step in eta1 the cells at the jump keep under a tenth
+    of the linear P3 weight, while cells whose stencils see only constant
+    data keep exactly the linear weight."""
+    mesh = inputs.jittered_mesh(24, 6, domain=(0.0, 1.0, 0.0, 0.25), seed=4, bc="periodic")
+    o = orc.Oracle(mesh, None, g=9.81, chi=0.5)
+    _, cx, _ = o.geometry()
+    avg = np.zeros((6, mesh.n_tri))
+    avg[3] = np.where((cx > 0.25) & (cx < 0.75), 0.7, 0.5)
+    avg[0] = 0.3
+    o.set_state(avg, np.zeros((6, 2, mesh.n_tri)))
+    o.reconstruct()
+    ratio = o.omega().reshape(mesh.n_tri, 6)[:, 3] / 0.85
+    dist = np.minimum(np.abs(cx - 0.25), np.abs(cx - 0.75))
+    at, away = dist < 0.03, dist >= 0.1
+    assert at.sum() >= 40 and away.sum() >= 150
+    assert ratio[at].max() < 0.1
+    assert np.abs(ratio[away] - 1).max() < 1e-12
