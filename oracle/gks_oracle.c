@@ -20,10 +20,12 @@
  * velocity/time quadrature, cubic reproduction, Gauss-theorem exactness,
  * uniform flux, lake at rest, conservation, convergence order). The blend
  * of Sec. 2.3 is pinned in its closed-form cases (xi = 1/2 at rest, xi = 0
- * or 1 in strong flow, against the two sides' point values). The WENO
- * constants (R5) and the edge weight w (R6) are not fixed by the paper: for
- * them parity is unpinned against the paper and fixed only by the readings
- * and the invariants above.
+ * or 1 in strong flow, against the two sides' point values) and the planes
+ * through the blended levels (exact for linear levels). The WENO constants
+ * (R5) and the form of the edge weight w (R6) are not fixed by the paper:
+ * for them parity is unpinned against the paper (parity unpinned), fixed by
+ * the readings and by the weights' pinned behaviour (exactly linear on
+ * smooth data, collapsing at a jump).
  */
 #include <math.h>
 #include <stdio.h>
