@@ -131,7 +131,9 @@ class Oracle:
         t = ctypes.c_double(0)
         st = lib().orc_advance(self._h, int(n_stages), float(t_end), ctypes.byref(t))
         if st != 0:
-            raise RuntimeError("oracle advance failed with status %d" % st)
+            why = {-10: "the CFL step is not a positive finite number (a non-physical state)",
+                   -11: "a non-finite interface state appeared in the stage"}.get(st, "unknown")
+            raise RuntimeError("oracle advance failed with status %d: %s" % (st, why))
         return t.value
 
     @property
