@@ -246,7 +246,7 @@ def test_trained_gate_gain_on_dambreak(trained):
     """What the gate gains on an unseen interface dam break (another seed and
     size than the training runs): the share of cells it lets skip the WENO
     weights, the reconstruction time saved, and the L1 change of the result
-    against the plain nonlinear reconstruction, which judges its error."""
+    against the plain nonlinear reconstruction, against which its error is measured."""
     P, _ = trained
     prob = inputs.interface_dambreak(256, seed=99)
     plain = g.problem_solver(prob, precision=g.GKS2L_FP32)
