@@ -596,3 +596,24 @@ def test_accuracy_test_errors_against_the_papers_table():
         ours = math.log2(errs[0, k] / errs[2, k]) / 2
         paper = math.log2(tab[0, col] / tab[2, col]) / 2
         assert abs(ours - paper) < 0.5, (ours, paper)
+
+
+def test_time_step_is_the_cfl_formula():
+    """Sec. 4: dt = CFL dX / U_max, U_max the larger over the layers of
+    |U| + sqrt(G h), dX the cell size (reading R10: the inscribed circle's
+    diameter 4|Omega|/perimeter, from the vertices here), minimised over the
+    cells; checked on a uniform two-layer flow where every term is known."""
+    mesh = inputs.jittered_mesh(9, 7, domain=(0.0, 1.0, 0.0, 0.8), seed=17, bc="periodic")
+    h1, h2, u1, v1, u2, v2 = 0.7, 0.3, 0.4, -0.3, 1.2, 0.5
+    avg = np.zeros((6, mesh.n_tri))
+    avg[:, :] = np.array([h2, h2 * u2, h2 * v2, h1, h1 * u1, h1 * v1])[:, None]
+    for cfl in (0.5, 0.2):
+        o = orc.Oracle(mesh, None, g=G, chi=0.9, cfl=cfl)
+        o.set_state(avg, np.zeros((6, 2, mesh.n_tri)))
+        o.advance(1)
+        p = mesh.xy[mesh.tri]
+        area = 0.5 * np.abs((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) -
+                            (p[:, 1, 1] - p[:, 0, 1]) * (p[:, 2, 0] - p[:, 0, 0]))
+        per = sum(np.hypot(*(p[:, (k + 1) % 3] - p[:, k]).T) for k in range(3))
+        umax = max(math.hypot(u1, v1) + math.sqrt(G * h1), math.hypot(u2, v2) + math.sqrt(G * h2))
+        assert abs(o.dt - cfl * (4 * area / per).min() / umax) < 1e-14
