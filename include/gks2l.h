@@ -40,12 +40,13 @@ extern "C" {
 #define GKS2L_EMESH -2       /* mesh not usable (orientation, periodic match, LS)   */
 #define GKS2L_ECUDA -3       /* a CUDA runtime call failed                          */
 #define GKS2L_ESTATE -4      /* call out of order (not bound, no state)             */
-#define GKS2L_ENEGDEPTH -5   /* a depth became <= 0 on the device                   */
+#define GKS2L_ENEGDEPTH -5   /* a depth is or became <= 0 on the device             */
 #define GKS2L_ENONFINITE -6  /* a non-finite value appeared on the device           */
 #define GKS2L_ESPACE -7      /* workspace too small                                 */
 #define GKS2L_ENOTIMPL -8
 #define GKS2L_ETOOBIG -9     /* size beyond a fixed maximum (gks2l_cfl_mass_noalloc) */
-#define GKS2L_ETIMEOUT -10   /* a bounded device wait (TMA staging) gave up        */
+#define GKS2L_ETIMEOUT -10   /* a bounded device wait (operator staging) gave up;  *
+                              * the stage's results are not valid                  */
 
 /* boundary kinds per triangle edge (edge k runs from tri[k] to tri[(k+1)%3]) */
 #define GKS2L_BC_INTERIOR 0
@@ -86,7 +87,13 @@ typedef struct {
  *   (1 + Q0^2). The paper defers both to an external reference.
  * precision: GKS2L_FP64 or GKS2L_FP32.
  * indicator, indicator_threshold: troubled-cell gate (GKS2L_INDICATOR_*); a
- *   cell is called smooth when the gate's output is below the threshold. */
+ *   cell is called smooth when the gate's output is below the threshold.
+ * staging_poll_limit: how long a reconstruction block waits for its operator
+ *   tile to arrive in shared memory. 0 (the default) waits up to about one
+ *   second; n > 0 polls at most n - 1 times, so 1 gives up at once. A block
+ *   that gives up records GKS2L_ETIMEOUT, waits once more (up to one second)
+ *   so that no copy outlives it, and writes nothing; a test sets 1 to raise
+ *   the code without a fault. */
 typedef struct {
   double g, chi, cfl;
   double eps, eps_num;
@@ -94,6 +101,7 @@ typedef struct {
   int32_t precision;
   int32_t indicator;
   float indicator_threshold;
+  int32_t staging_poll_limit;
 } gks2l_params;
 
 /* Run statistics (FP64 sums taken on the device). */
@@ -263,18 +271,24 @@ int gks2l_alu_peaks(gks2l_ctx *ctx, double tflops[2]);
  * computes what the library's own CFL kernel computes for a bound context
  * (Sec. 4: dt = CFL * min_j dX_j / U_max,j, U_max = max over layers of
  * |U| + sqrt(G h); plus sum_j |Omega_j| h_j per layer), with its scratch in a
- * fixed device array of 3 x 1024 doubles (24 KB) that every GPU loading the
+ * fixed device array of 4 x 1024 doubles (32 KB) that every GPU loading the
  * library holds until the process exits.
  *   n_tri   number of cells, 1 .. GKS2L_NOALLOC_MAX_TRI (larger: GKS2L_ETOOBIG)
  *   d_avg   device, 6*n_tri doubles, variable-major state (any cell order)
  *   d_area  device, n_tri cell areas, d_dX device, n_tri CFL lengths
  *           (4 |Omega| / perimeter), both in the same cell order as d_avg
- *   d_out   device, 3 doubles written: dt, mass of layer 1 (lower), mass of
- *           layer 2
+ *   d_out   device, 4 doubles written: dt, mass of layer 1 (lower), mass of
+ *           layer 2, and the number of unusable cells (a depth <= 0 or a
+ *           non-finite speed or CFL ratio); those cells take no part in dt
+ *           (dt = inf if every cell is unusable), so a caller checks d_out[3]
+ *           before trusting dt
  *   stream  cudaStream_t (NULL = default stream); the call only enqueues work.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. All calls share the one array, so calls whose
+ * before any stream capture. The address is kept for the life of the
+ * process: after a cudaDeviceReset of that device it is stale, so calls after
+ * a reset are not supported (they would launch kernels on an unmapped
+ * address). All calls share the one array, so calls whose
  * work overlaps on the GPU (other streams, other threads) race; serialise
  * them. Nothing in the array needs clearing: each call overwrites the slots it
  * reads. Calls no cudaMalloc, cudaFree or allocating library routine. */

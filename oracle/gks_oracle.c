@@ -9,7 +9,7 @@
  * baseline may load it. It shares no code with the CUDA library.
  *
  * Every routine follows the paper's steps in its notation; where the paper is
- * silent the reading is named (R1..R15) and listed with its reason in the
+ * silent the reading is named (R1..R20) and listed with its reason in the
  * repository's design notes. Build: gcc -O2 -ffp-contract=off -fPIC -shared.
  *
  * Variable order per cell (Sec. 2.1, Eq. SWE-macro): h2, h2U2, h2V2, h1, h1U1,
@@ -977,7 +977,11 @@ static void to_local_side(const double val[NVAR], const double grd[NVAR][2], int
 
 static void stage(orc_t *o, int st) {
   const double dt = o->dt;
-  const double delta = (st == 1) ? dt : 0.5 * dt;   /* stage interval (Sec. 3.3, S2O4) */
+  /* the fit interval (reading R20): both stages fit the value and time     */
+  /* derivative at their start from the time integrals over dt and dt/2   */
+  /* (the S2O4 construction of Sec. 3.3 repeated from the intermediate    */
+  /* state)                                                                */
+  const double delta = dt;
   const double G = o->g;
   reconstruct(o);
   /* interface values at each Gauss point, both sides (R3, R7) */
@@ -1107,7 +1111,7 @@ static void stage(orc_t *o, int st) {
       }
     }
   }
-  free(vl); free(vr); free(gl); free(gr);
+  free(gl); free(gr);
   if (st == 1) memcpy(o->eWn, o->eW, sizeof(double) * ne * 2 * NVAR);
   /* cell residuals and update */
   double *newavg = malloc(sizeof(double) * o->nt * NVAR);
@@ -1115,8 +1119,11 @@ static void stage(orc_t *o, int st) {
   for (int j = 0; j < o->nt; j++) {
     double A = o->area[j];
     double LF[NVAR] = {0}, LFt[NVAR] = {0};
-    double mW[NVAR] = {0}, mWt[NVAR] = {0};         /* mean over the 6 Gauss points */
-    double GG[NVAR][2] = {{0}}, GGt[NVAR][2] = {{0}}, GGn[NVAR][2] = {{0}};
+    double mWt[NVAR] = {0};                          /* mean over the 6 Gauss points */
+    double GGt[NVAR][2] = {{0}}, GGn[NVAR][2] = {{0}};
+    /* the cell's own reconstruction at its six Gauss points (reading R16):   */
+    /* the mean of h over them and their Gauss-theorem gradient               */
+    double mO[NVAR] = {0}, GO[NVAR][2] = {{0}};
     for (int f = 0; f < 3; f++) {
       int e = o->face_edge[IDX2(j, f)];
       double sg = o->face_side[IDX2(j, f)];
@@ -1124,16 +1131,17 @@ static void stage(orc_t *o, int st) {
       for (int q = 0; q < 2; q++) {
         for (int v = 0; v < NVAR; v++) {
           double F = o->eF[(e * 2 + q) * NVAR + v], Ft = o->eFt[(e * 2 + q) * NVAR + v];
-          double W = o->eW[(e * 2 + q) * NVAR + v], Wt = o->eWt[(e * 2 + q) * NVAR + v];
+          double Wt = o->eWt[(e * 2 + q) * NVAR + v];
           double Wn = o->eWn[(e * 2 + q) * NVAR + v];
+          double Wo = sg > 0 ? vl[e][q][v] : vr[e][q][v];   /* this cell's side */
           LF[v] -= sg * E->len * 0.5 * F / A;          /* Eq. SWE-semi-flux */
           LFt[v] -= sg * E->len * 0.5 * Ft / A;
-          mW[v] += W / 6;
+          mO[v] += Wo / 6;
           mWt[v] += Wt / 6;
           /* interface value at the stage end (Eq. S2O3) */
           double Wend = (st == 1) ? Wn + 0.5 * dt * Wt : Wn + dt * Wt;
           for (int d = 0; d < 2; d++) {
-            GG[v][d] += sg * E->len * E->n[d] * 0.5 * W / A;      /* Gauss theorem (Eq. slope-1) */
+            GO[v][d] += sg * E->len * E->n[d] * 0.5 * Wo / A;     /* Gauss theorem (Eq. slope-1) */
             GGt[v][d] += sg * E->len * E->n[d] * 0.5 * Wt / A;
             GGn[v][d] += sg * E->len * E->n[d] * 0.5 * Wend / A;
           }
@@ -1152,14 +1160,17 @@ static void stage(orc_t *o, int st) {
         Lt[b + 1 + d] += -G * LF[b] * gB[d];
       }
     }
-    /* interlayer source L^S2 (Eq. SWE-source-discretization), reading R4 */
+    /* interlayer source L^S2 (Eq. SWE-source-discretization): the point     */
+    /* values are the cell's own reconstruction at its six Gauss points      */
+    /* (reading R16); the time derivative by the product rule with the       */
+    /* interface solution's time derivatives W_t (reading R4)                */
     for (int d = 0; d < 2; d++) {
       /* upper: -G mean(h2) * GaussGrad(h1) */
-      L[1 + d] += -G * mW[0] * GG[3][d];
-      Lt[1 + d] += -G * (mWt[0] * GG[3][d] + mW[0] * GGt[3][d]);
+      L[1 + d] += -G * mO[0] * GO[3][d];
+      Lt[1 + d] += -G * (mWt[0] * GO[3][d] + mO[0] * GGt[3][d]);
       /* lower: -chi G mean(h1) * GaussGrad(h2) */
-      L[4 + d] += -o->chi * G * mW[3] * GG[0][d];
-      Lt[4 + d] += -o->chi * G * (mWt[3] * GG[0][d] + mW[3] * GGt[0][d]);
+      L[4 + d] += -o->chi * G * mO[3] * GO[0][d];
+      Lt[4 + d] += -o->chi * G * (mWt[3] * GO[0][d] + mO[3] * GGt[0][d]);
     }
     for (int v = 0; v < NVAR; v++) {
       if (st == 1) {
@@ -1177,6 +1188,7 @@ static void stage(orc_t *o, int st) {
   memcpy(o->avg, newavg, sizeof(double) * o->nt * NVAR);
   memcpy(o->grad, newgrad, sizeof(double) * o->nt * NVAR * 2);
   free(newavg); free(newgrad);
+  free(vl); free(vr);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -37,6 +37,7 @@ constexpr unsigned long long DBL_INF_BITS = 0x7FF0000000000000ull;
 constexpr int TW = 32;                  // cells per reconstruction tile
 constexpr int REF_CHUNK = 4096;         // cells per chunk of the reference-level reduction
 constexpr int ST_TIMEOUT = 4;           // status bit: a bounded wait gave up
+constexpr int ST_COPY_LOST = 8;         // status bit: the second wait gave up too (copies in flight)
 constexpr int GATE_LD = 40;             // padded row stride of the gate feature tile (bank spread)
 
 // ---------------------------------------------------------------- TMA staging
@@ -92,9 +93,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // wait for the phase of the given parity of an mbarrier for at most ~limit_ns
-__device__ __forceinline__ bool mbar_wait_bounded(void *bar, unsigned parity, unsigned long long limit_ns) {
+// and at most max_polls polls
+__device__ __forceinline__ bool mbar_wait_bounded(void *bar, unsigned parity, unsigned long long limit_ns,
+                                                  int max_polls = 1 << 24) {
   unsigned long long t0 = global_ns();
-  for (int it = 0; it < (1 << 24); it++) {
+  for (int it = 0; it < max_polls; it++) {
     if (mbar_try_wait(bar, parity)) return true;
     if (global_ns() - t0 > limit_ns) return false;
   }
@@ -137,12 +140,15 @@ __global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p)
   const int j = j0 + threadIdx.x, v = threadIdx.y;
   const bool active = j < d.nt && (p.all_active || d.dt[d.inst[j]] > 0);
   __syncthreads();
-  const bool landed = mbar_wait_bounded(bar, 0, 1000000000ull);
+  const bool landed =
+      mbar_wait_bounded(bar, 0, 1000000000ull, p.staging_polls > 0 ? p.staging_polls - 1 : (1 << 24));
   if (!__syncthreads_and(landed)) {
-    // the copies did not land within a second: report, wait for them once
-    // more (bounded) so no copy outlives the block, and leave (all threads)
+    // the copies did not land in time: report, wait for them once more
+    // (bounded, a second) so no copy outlives the block, and leave (all
+    // threads); if they still have not landed, the block's shared memory may
+    // yet be written after it exits, which a second bit records
     if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(d.status, ST_TIMEOUT);
-    if (!landed) mbar_wait_bounded(bar, 0, 1000000000ull);
+    if (!landed && !mbar_wait_bounded(bar, 0, 1000000000ull)) atomicOr(d.status, ST_COPY_LOST);
     return;
   }
   CellOps<R> o;
@@ -261,17 +267,29 @@ __global__ void k_harvest(Dev d, const int *perm, float tol, const float *logit_
   if (logits) logits[c] = logit_dev[j];
 }
 
+// Each side's own level of layer ell, the mean over the edge's two points:
+// the q = 0 thread writes the L side's, the q = 1 thread the R side's.
+template <typename R>
+__device__ __forceinline__ void own_write(const Dev &d, int e, int ell, int q, const R own[2], bool ok) {
+  const R mine = q == 0 ? own[0] : own[1], theirs = q == 0 ? own[1] : own[0];
+  const R m = (R)0.5 * (mine + __shfl_xor_sync(FULL, theirs, 1));
+  if (ok) ((R *)d.eO)[(2 * q + ell) * d.ne + e] = m;
+}
+
 // An edge's results for layer ell: the Gauss point q = 0 thread holds the
 // averaged F and F_t, the q = 1 thread W and W_t (avg[0..2], avg[3..5]). The
 // depth components of F and F_t also go out in FP64 for the cells' mass sums.
+// Stage 2 keeps only W_t: the stage-end interface values take the stage-1
+// W^n(x) (Eq. S2O3) and the interlayer source the cells' own levels.
 template <typename R>
 __device__ __forceinline__ void edge_write(const Dev &d, int e, int ell, int q, int stage, const R avg[6]) {
   const int NE = d.ne;
   const int vb = ell == 0 ? 3 : 0;
-  R *A = (R *)(q == 0 ? d.eF : (stage == 1 ? d.eWn : d.eW));
+  R *A = (R *)(q == 0 ? d.eF : d.eWn);
   R *B = (R *)(q == 0 ? d.eFt : d.eWt);
+  const bool wa = q == 0 || stage == 1;
   for (int k = 0; k < 3; k++) {
-    A[(vb + k) * NE + e] = avg[k];
+    if (wa) A[(vb + k) * NE + e] = avg[k];
     B[(vb + k) * NE + e] = avg[3 + k];
   }
   if (q == 0) {
@@ -296,9 +314,10 @@ __device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage)
   // every thread computes (past the last edge: the last edge again), before
   // its instance's dt is known, so the unit's loads issue at once; only
   // edges of instances still running are written
-  R out[12];
-  edge_unit<R>(d, p, ee, ell, q, stage, out);
+  R out[12], own[2];
+  edge_unit<R>(d, p, ee, ell, q, stage, out, nullptr, own);
   const bool ok = e < d.ne && d.dt[d.inst[d.eL[ee]]] > 0;
+  own_write<R>(d, e, ell, q, own, ok);
   // the Gauss point q = 0 thread averages the fluxes (out[0..5]), the q = 1
   // thread the interface values (out[6..11]): each sends the other its half
   R avg[6];
@@ -321,8 +340,8 @@ __device__ __forceinline__ void edge_fused_body(const Dev &d, const Par &p, int 
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   int e = tid >> 2, ell = (tid >> 1) & 1, q = tid & 1;
   const int ee = e < d.ne ? e : d.ne - 1;
-  R out[12], bl = 0;
-  const bool done = edge_unit<R, true>(d, p, ee, ell, q, stage, out, &bl);
+  R out[12], bl = 0, own[2];
+  const bool done = edge_unit<R, true>(d, p, ee, ell, q, stage, out, &bl, own);
   if (!done) {
     for (int k = 0; k < 12; k++) out[k] = 0;
   }
@@ -337,6 +356,7 @@ __device__ __forceinline__ void edge_fused_body(const Dev &d, const Par &p, int 
     avg[k] = (R)0.5 * (mine + __shfl_xor_sync(FULL, theirs, 1));
   }
   const bool ok = e < d.ne && d.dt[d.inst[d.eL[ee]]] > 0;
+  own_write<R>(d, e, ell, q, own, ok);
   // deferred units to the worklist, one atomic per warp
   const bool push = ok && q == 0 && !done;
   const unsigned bal = __ballot_sync(FULL, push);
@@ -479,23 +499,29 @@ __global__ void __launch_bounds__(128, 4) k_edgef_r128(Dev d, Par p, int stage) 
 template <typename R>
 __global__ void __launch_bounds__(128, 4) k_update_r128(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
 
-// CFL ratio of the current state (after a state is set)
+// CFL ratio of the current state (after a state is set), in the form's
+// precision as the update kernel computes it; a depth <= 0 or a non-finite
+// value is recorded
+template <typename R>
 __global__ void __launch_bounds__(128) k_cfl(Dev d, Par p) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   bool ok = j < d.nt;
   int inst = ok ? d.inst[j] : 0;
   double ratio = INFINITY;
   if (ok) {
-    double um = 0;
-    for (int l = 0; l < 2; l++) {
-      double h = d.avg[(3 * l) * d.cs + j];
-      double u = d.avg[(3 * l + 1) * d.cs + j] / h, v = d.avg[(3 * l + 2) * d.cs + j] / h;
-      double sp = sqrt(u * u + v * v) + sqrt(p.g * h);
-      um = fmax(um, sp);
+    double w[NV];
+    int fl = 0;
+    for (int v = 0; v < NV; v++) {
+      w[v] = d.avg[v * d.cs + j];
+      if (!isfinite(w[v])) fl = 2;
     }
-    ratio = d.dX[j] / um;
-    if (!(ratio > 0) || !isfinite(ratio)) {
-      atomicOr(d.status, 2);
+    if (!fl && (w[0] <= 0 || w[3] <= 0)) fl = 1;
+    if (!fl) {
+      ratio = cfl_ratio<R>(w, d.dX[j], pv<R>(p.g, p.gf));
+      if (!(ratio > 0) || !isfinite(ratio)) fl = 2;
+    }
+    if (fl) {
+      atomicOr(d.status, fl);
       ratio = INFINITY;
     }
   }
@@ -576,7 +602,7 @@ __global__ void k_step_begin(Dev d, Par p, const double *tend) {
 }
 
 // deviation mirrors of a freshly set state: dq, dg (gradients given in the
-// caller's order, grad h1 -> grad eta1 = grad h1 + grad B), R1 - B per cell
+// caller's order, stored as given), R1 - B per cell
 template <typename R>
 __global__ void k_mirrors(Dev d, const int *perm, const double *grad_caller) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -587,12 +613,7 @@ __global__ void k_mirrors(Dev d, const int *perm, const double *grad_caller) {
   dq[j] = (R)(d.avg[j] - R2);
   dq[3 * N + j] = (R)((d.avg[3 * N + j] + d.bmean[j]) - R1);
   for (int v : {1, 2, 4, 5}) dq[v * N + j] = (R)d.avg[v * N + j];
-  for (int k = 0; k < 12; k++) {
-    double gk = grad_caller ? grad_caller[(size_t)k * d.nt + c] : 0.0;
-    if (k == 6) gk += d.bgx[j];
-    if (k == 7) gk += d.bgy[j];
-    dg[k * N + j] = (R)gk;
-  }
+  for (int k = 0; k < 12; k++) dg[k * N + j] = (R)(grad_caller ? grad_caller[(size_t)k * d.nt + c] : 0.0);
   ((R *)d.hrefc)[j] = (R)(R1 - d.bmean[j]);
 }
 
@@ -605,19 +626,14 @@ __global__ void k_edge_ref(Dev d) {
   ((R *)d.hrefe)[d.ne + e] = (R)(R1 - d.eb1[e]);
 }
 
-// gradients in the caller's order, grad eta1 -> grad h1
+// gradients in the caller's order
 template <typename R>
 __global__ void k_grad_out(Dev d, const int *perm, double *out) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= d.nt) return;
   const int c = perm[j];
   const R *dg = (const R *)d.dg;
-  for (int k = 0; k < 12; k++) {
-    double gk = (double)dg[k * d.cs + j];
-    if (k == 6) gk -= d.bgx[j];
-    if (k == 7) gk -= d.bgy[j];
-    out[(size_t)k * d.nt + c] = gk;
-  }
+  for (int k = 0; k < 12; k++) out[(size_t)k * d.nt + c] = (double)dg[k * d.cs + j];
 }
 
 // caller order (stride nt) <-> device order (stride cs)
@@ -752,7 +768,7 @@ size_t layout(gks2l_ctx *c, char *base) {
   d.eFt = k.take<char>(rs * 6 * ne);
   d.eFm = k.take<double>(2 * ne);
   d.eFtm = k.take<double>(2 * ne);
-  d.eW = k.take<char>(rs * 6 * ne);
+  d.eO = k.take<char>(rs * 4 * ne);
   d.eWt = k.take<char>(rs * 6 * ne);
   d.eWn = k.take<char>(rs * 6 * ne);
   d.ref = k.take<double>(2 * ni);
@@ -873,6 +889,7 @@ Par make_par(const gks2l_ctx *c) {
   p.harvest = 0;
   p.logit_out = nullptr;
   p.all_active = 0;
+  p.staging_polls = c->par.staging_poll_limit;
   return p;
 }
 
@@ -992,10 +1009,12 @@ int ensure_graph(gks2l_ctx *c) {
   return 0;
 }
 
+// a staging timeout first: the stages after it computed from stale records,
+// so the non-finite values or depths they may show are its consequence
 int status_code(int st) {
+  if (st & (ST_TIMEOUT | ST_COPY_LOST)) return GKS2L_ETIMEOUT;
   if (st & 2) return GKS2L_ENONFINITE;
   if (st & 1) return GKS2L_ENEGDEPTH;
-  if (st & ST_TIMEOUT) return GKS2L_ETIMEOUT;
   return 0;
 }
 
@@ -1031,7 +1050,8 @@ int after_state(gks2l_ctx *c, const double *grad_caller) {
   CK(cudaMemsetAsync(c->d.gate_count, 0, 2 * sizeof(unsigned long long), c->stream));
   // no gate decisions yet: the first reconstruction is the plain one
   CK(cudaMemsetAsync(c->d.gate_mask, 0, (c->cs / TW) * sizeof(unsigned), c->stream));
-  k_cfl<<<blocks(c->d.nt, 128), 128, 0, c->stream>>>(c->d, p);
+  if (c->par.precision == GKS2L_FP32) k_cfl<float><<<blocks(c->d.nt, 128), 128, 0, c->stream>>>(c->d, p);
+  else k_cfl<double><<<blocks(c->d.nt, 128), 128, 0, c->stream>>>(c->d, p);
   CK(cudaGetLastError());
   c->phase = 0;
   c->stages = 0;
@@ -1046,7 +1066,7 @@ int create_impl(int n, const gks2l_mesh *meshes, const gks2l_params *params, gks
   else gks2l_default_params(&c->par);
   if (!(c->par.g > 0) || !(c->par.cfl > 0) || !(c->par.eps > 0) || c->par.eps_num < 0 || !(c->par.chi > 0) ||
       !(c->par.weno_gamma_hi > 0 && c->par.weno_gamma_hi <= 1) || c->par.weno_eps < 0 ||
-      (c->par.precision != GKS2L_FP64 && c->par.precision != GKS2L_FP32)) {
+      (c->par.precision != GKS2L_FP64 && c->par.precision != GKS2L_FP32) || c->par.staging_poll_limit < 0) {
     delete c;
     return GKS2L_EINVAL;
   }
@@ -1077,6 +1097,7 @@ int gks2l_default_params(gks2l_params *p) {
   p->precision = GKS2L_FP64;
   p->indicator = GKS2L_INDICATOR_OFF;
   p->indicator_threshold = 0.5f;
+  p->staging_poll_limit = 0;
   return GKS2L_OK;
 }
 

@@ -10,7 +10,9 @@
 // 2^-32. The kernels read and write only deviations from them, of type R
 // (double in the FP64 form, float in the FP32 form): the cell mirrors
 // dq = (h2 - R2, h2U2, h2V2, eta1 - R1, h1U1, h1V1) and gradients
-// dg = grad(h2, h2U2, h2V2, eta1, h1U1, h1V1). At rest (eta1 and h2 constant,
+// dg = grad(h2, h2U2, h2V2, h1, h1U1, h1V1), the state's own gradients (so a
+// state read out and set again is the same bit for bit); the reconstruction
+// sees grad eta1 = grad h1 + grad B of each cell. At rest (eta1 and h2 constant,
 // Sec. 3.2) every deviation vanishes, so the well-balanced cancellation
 // between the interface flux and the cell sources holds in any precision: the
 // reference pressure G (R1 - B)^2 / 2 of the lower layer is integrated around
@@ -87,7 +89,9 @@ struct Dev {
   void *hc;                 // [2][edge] edge-centre blended level deviations, type R
   int *wl;                  // [2 * edge] (edge << 1 | layer) units left to the deferred edge pass
   int *wl_count;            // their number (zeroed before each fused edge launch)
-  void *eF, *eFt, *eW, *eWt, *eWn;  // [6][edge] Gauss-point sums (weights 1/2), deviations, type R
+  void *eF, *eFt, *eWt, *eWn;  // [6][edge] Gauss-point sums (weights 1/2), deviations, type R
+  void *eO;                 // [side][layer][edge] each side's own level deviation, mean over
+                            // the two Gauss points (the interlayer source's point values)
   double *eFm, *eFtm;       // [2][edge] the depth components of F, F_t (h2 first, then eta1) in
                             // FP64, converted once per edge for the cells' FP64 mass sums
   // per instance
@@ -109,6 +113,7 @@ struct Par {
   float *logit_out;                          // gate logits per cell (device order), or null
   int all_active;                            // reconstruct every instance (harvesting)
   int harvest;                               // record the weights' departure from linear
+  int staging_polls;                         // > 0: operator staging polls at most this many - 1 times
 };
 
 // a parameter in the form's precision
@@ -186,23 +191,23 @@ __host__ __device__ __forceinline__ R img_dq(const Dev &d, int v, int c, int xf)
   rot2<R>(d.xf + 4 * xf, m);
   return m[v - b];
 }
-// gradient of variable v of cell c seen through transform xf
+// gradient of reconstructed variable v of cell c seen through transform xf
+// (for v = 3 the water level's: the stored grad h1 plus the cell's grad B)
 template <typename R>
 __host__ __device__ __forceinline__ void img_dg(const Dev &d, int v, int c, int xf, R g[2]) {
   const int N = d.cs;
   const R *G = (const R *)d.dg;
-  if (xf == 0) {
+  if (v == 0 || v == 3 || xf == 0) {
     g[0] = G[(2 * v) * N + c];
     g[1] = G[(2 * v + 1) * N + c];
+    if (v == 3) {
+      g[0] += ((const R *)d.bgR)[c];
+      g[1] += ((const R *)d.bgR)[N + c];
+    }
+    if (xf != 0) rot2<R>(d.xf + 4 * xf, g);
     return;
   }
   const double *M = d.xf + 4 * xf;
-  if (v == 0 || v == 3) {
-    g[0] = G[(2 * v) * N + c];
-    g[1] = G[(2 * v + 1) * N + c];
-    rot2<R>(M, g);
-    return;
-  }
   // discharge gradient tensor T_ik = d m_i / d x_k -> M T M^T, row v - b
   int b = v < 3 ? 1 : 4;
   int row = v - b;
@@ -785,12 +790,16 @@ __host__ __device__ __forceinline__ void plane_grad(const Dev &d, int c, int whi
 // gradients gathered).
 template <typename R, bool FUSED = false>
 __host__ __device__ inline bool edge_unit(const Dev &d, const Par &p, int e, int ell, int q, int stage, R out[12],
-                                          R *blend = nullptr) {
+                                          R *blend = nullptr, R *own = nullptr) {
   const int NE = d.ne;
   const R *xl = (const R *)d.exiL, *xr = (const R *)d.exiR, *en = (const R *)d.en;
   int cL = d.eL[e], cR = d.eR[e], xf = d.exf[e];
   const R dt = ((const R *)d.dtR)[d.inst[cL]];
-  const R delta = stage == 1 ? dt : (R)0.5 * dt;
+  // both stages fit the value and time derivative at their start from the
+  // time integrals over dt and dt/2 (the S2O4 construction repeated from the
+  // intermediate state, reading R20)
+  const R delta = dt;
+  (void)stage;
   const R href = ref_depth<R>(d, ell, e, q);
   SideVals<R> s[2];
   side_vals<R>(d, ell, cL, 0, xl[(2 * q) * NE + e], xl[(2 * q + 1) * NE + e], href, s[0]);
@@ -834,6 +843,11 @@ __host__ __device__ inline bool edge_unit(const Dev &d, const Par &p, int e, int
       outv[k][2] = -dmx * n1 + dmy * n0;
     }
   }
+  // each side's own level at the point: the interlayer source's values (R16)
+  if (own) {
+    own[0] = s[0].d;
+    own[1] = s[1].d;
+  }
   if (FUSED) {
     *blend = blend_level<R>(s[0].d, s[0].h, s[0].mx, s[0].my, s[1].d, s[1].h, s[1].mx, s[1].my, n0, n1);
     if (w < (R)1) return false;
@@ -855,6 +869,23 @@ __host__ __device__ inline bool edge_unit(const Dev &d, const Par &p, int e, int
 }
 
 // ------------------------------------------------------------- cell unit
+// dX / U_max of a cell state w (Sec. 4: U_max the larger over the layers of
+// |U| + sqrt(G h)) in the form's precision; the update kernel and the kernel
+// that starts a newly set state both use it, so a restarted run takes the
+// same steps as an uninterrupted one. FP32 form: the reciprocal in single
+// precision (dt to ~1e-7 relative), sparing the FP64 pipe a double division.
+template <typename R>
+__host__ __device__ inline double cfl_ratio(const double w[NV], double dX, R G) {
+  R um = 0;
+  for (int l = 0; l < 2; l++) {
+    R h = (R)w[3 * l], u = (R)w[3 * l + 1] / h, v = (R)w[3 * l + 2] / h;
+    R sp = r_sqrt<R>(u * u + v * v) + r_sqrt<R>(G * h);
+    um = sp > um ? sp : um;
+  }
+  if (sizeof(R) == 4) return dX * (double)((R)1 / um);
+  return dX / (double)um;
+}
+
 // Flux and source residuals, S2O4 update (Eq. SWE-fully-discrete), interface
 // values at the stage end (Eq. S2O3) and Gauss-theorem gradients (Eq. slope-1).
 // Returns the CFL ratio dX/U_max of the new state (stage 2) or 0.
@@ -867,34 +898,42 @@ __host__ __device__ inline double update_unit(const Dev &d, const Par &p, int j,
   // that has stopped (dt = 0) is computed too, and only its writes are dropped
   const bool act = dt > 0;
   const R *eF = (const R *)d.eF, *eFt = (const R *)d.eFt, *eWt = (const R *)d.eWt, *eWn = (const R *)d.eWn;
-  const R *Wcur = stage == 1 ? eWn : (const R *)d.eW;
+  const R *eO = (const R *)d.eO;
   const R *en = (const R *)d.en;
   const R dtr = ((const R *)d.dtR)[in];
   const R cend = stage == 1 ? (R)0.5 * dtr : dtr;
   // mass residuals in FP64 (exact conservation), the rest in R
   double LFm[2] = {0, 0}, LFtm[2] = {0, 0};
-  R LF[NV] = {0}, LFt[NV] = {0}, mW[NV] = {0}, mWt[NV] = {0};
-  R GG[NV][2] = {{0}}, GGt[NV][2] = {{0}}, GGn[NV][2] = {{0}};
+  R LF[NV] = {0}, LFt[NV] = {0}, mWt[NV] = {0};
+  R GGt[NV][2] = {{0}}, GGn[NV][2] = {{0}};
+  // the interlayer source's point values (R16): this cell's own levels at its
+  // six Gauss points, their mean (mO) and Gauss-theorem gradient (GO), for
+  // the lower (0: eta1 - R1) and upper (1: h2 - R2) layer
+  R mO[2] = {0, 0}, GO[2][2] = {{0, 0}, {0, 0}};
   for (int f = 0; f < 3; f++) {
     int ce = d.cedge[f * N + j];
     int e = ce >= 0 ? ce : ~ce;
+    const int side = ce >= 0 ? 0 : 2;
     const double sl = d.fsl[f * N + j];
     const R slR = ((const R *)d.fslR)[f * N + j];
     const R nx = en[e], ny = en[NE + e];
+    const R snx = slR * nx, sny = slR * ny;
+    for (int l = 0; l < 2; l++) {
+      const R o = eO[(side + l) * NE + e];
+      mO[l] += o * (R)(1.0 / 3.0);
+      GO[l][0] += snx * o; GO[l][1] += sny * o;
+    }
     for (int v = 0; v < NV; v++) {
-      R W = Wcur[v * NE + e], Wt = eWt[v * NE + e], Wn = eWn[v * NE + e];
+      R Wt = eWt[v * NE + e], Wn = eWn[v * NE + e];
       if (v == 0 || v == 3) {
         LFm[v / 3] -= sl * d.eFm[(v / 3) * NE + e];
         LFtm[v / 3] -= sl * d.eFtm[(v / 3) * NE + e];
+        mWt[v] += Wt * (R)(1.0 / 3.0);
+        GGt[v][0] += snx * Wt; GGt[v][1] += sny * Wt;
       } else {
         LF[v] -= slR * eF[v * NE + e];
         LFt[v] -= slR * eFt[v * NE + e];
       }
-      mW[v] += W * (R)(1.0 / 3.0);
-      mWt[v] += Wt * (R)(1.0 / 3.0);
-      R snx = slR * nx, sny = slR * ny;
-      GG[v][0] += snx * W; GG[v][1] += sny * W;
-      GGt[v][0] += snx * Wt; GGt[v][1] += sny * Wt;
       R We = Wn + cend * Wt;
       GGn[v][0] += snx * We; GGn[v][1] += sny * We;
     }
@@ -904,16 +943,17 @@ __host__ __device__ inline double update_unit(const Dev &d, const Par &p, int j,
   const R *dq = (const R *)d.dq;
   const R R2 = ((const R *)d.refR)[2 * in];
   const R hrc = ((const R *)d.hrefc)[j];          // R1 - B_j
-  const R m1 = hrc + mW[3], m2 = R2 + mW[0];       // means of h1, h2 over the 6 Gauss points
+  const R m1 = hrc + mO[0], m2 = R2 + mO[1];       // means of h1, h2 over the 6 Gauss points
   const R LFh2 = (R)LFm[0], LFh1 = (R)LFm[1];
   R L[NV], Lt[NV];
   for (int k = 0; k < 2; k++) {
-    // upper layer: -G h2 grad(B + h1) with the interface h1 = eta1 - B
-    L[1 + k] = LF[1 + k] - G * (dq[j] - mW[0]) * gb[k] - G * m2 * GG[3][k];
-    Lt[1 + k] = LFt[1 + k] - G * (LFh2 - mWt[0]) * gb[k] - G * mWt[0] * GG[3][k] - G * m2 * GGt[3][k];
+    // upper layer: -G h2 grad(B + h1) with h1 = eta1 - B at the points; the
+    // time derivative by the product rule with the interface solution's W_t (R4)
+    L[1 + k] = LF[1 + k] - G * (dq[j] - mO[1]) * gb[k] - G * m2 * GO[0][k];
+    Lt[1 + k] = LFt[1 + k] - G * (LFh2 - mWt[0]) * gb[k] - G * mWt[0] * GO[0][k] - G * m2 * GGt[3][k];
     // lower layer: flux reference pressure + bottom source -> -G (eta1 - R1) grad B; interlayer -chi G h1 grad h2
-    L[4 + k] = LF[4 + k] - G * dq[3 * N + j] * gb[k] - chi * G * m1 * GG[0][k];
-    Lt[4 + k] = LFt[4 + k] - G * LFh1 * gb[k] - chi * G * (mWt[3] * GG[0][k] + m1 * GGt[0][k]);
+    L[4 + k] = LF[4 + k] - G * dq[3 * N + j] * gb[k] - chi * G * m1 * GO[1][k];
+    Lt[4 + k] = LFt[4 + k] - G * LFh1 * gb[k] - chi * G * (mWt[3] * GO[1][k] + m1 * GGt[0][k]);
   }
   // S2O4 (Eq. SWE-fully-discrete): stage 1 W* = W^n + dt/2 L^n + dt^2/8 L_t^n;
   // stage 2 W^{n+1} = W^n + dt L^n + dt^2/6 L_t^n + dt^2/3 L_t^*. The layer
@@ -955,8 +995,9 @@ __host__ __device__ inline double update_unit(const Dev &d, const Par &p, int j,
     R *dqw = (R *)d.dq, *dgw = (R *)d.dg;
     for (int v = 0; v < NV; v++) {
       d.avg[v * N + j] = nw[v];
-      dgw[(2 * v) * N + j] = GGn[v][0];
-      dgw[(2 * v + 1) * N + j] = GGn[v][1];
+      // the interface values of variable 3 are water levels: grad h1 = grad eta1 - grad B
+      dgw[(2 * v) * N + j] = v == 3 ? GGn[v][0] - gb[0] : GGn[v][0];
+      dgw[(2 * v + 1) * N + j] = v == 3 ? GGn[v][1] - gb[1] : GGn[v][1];
     }
     dqw[j] = (R)(nw[0] - d.ref[2 * in]);
     dqw[3 * N + j] = (R)((nw[3] + d.bmean[j]) - d.ref[2 * in + 1]);
@@ -969,16 +1010,7 @@ __host__ __device__ inline double update_unit(const Dev &d, const Par &p, int j,
   if (!(dbits(nw[0]) > 0) || !(dbits(nw[3]) > 0)) fl |= 1;
   *flags = act ? fl : 0;
   if (stage != 2 || !act) return 0;
-  R um = 0;
-  for (int l = 0; l < 2; l++) {
-    R h = (R)nw[3 * l], u = (R)nw[3 * l + 1] / h, v = (R)nw[3 * l + 2] / h;
-    R sp = r_sqrt<R>(u * u + v * v) + r_sqrt<R>(G * h);
-    um = sp > um ? sp : um;
-  }
-  // FP32 form: the reciprocal in single precision (dt to ~1e-7 relative),
-  // sparing the FP64 pipe a double division; FP64 form: exact
-  if (sizeof(R) == 4) return d.dX[j] * (double)((R)1 / um);
-  return d.dX[j] / (double)um;
+  return cfl_ratio<R>(nw, d.dX[j], G);
 }
 
 }  // namespace gks2l

@@ -24,6 +24,18 @@ GKS2L_BC_WALL = 1
 GKS2L_BC_PERIODIC = 2
 GKS2L_MLP_NPARAM = 1937
 GKS2L_MLP_NTRAIN = 1889
+GKS2L_OK = 0
+GKS2L_EINVAL = -1
+GKS2L_EMESH = -2
+GKS2L_ECUDA = -3
+GKS2L_ESTATE = -4
+GKS2L_ENEGDEPTH = -5
+GKS2L_ENONFINITE = -6
+GKS2L_ESPACE = -7
+GKS2L_ENOTIMPL = -8
+GKS2L_ETOOBIG = -9
+GKS2L_ETIMEOUT = -10
+GKS2L_LAUNCH_SHAPES = 5
 
 # every entry point the header declares, with (restype, argtypes)
 _P = ctypes.c_void_p
@@ -39,7 +51,8 @@ class gks2l_mesh(ctypes.Structure):
 class gks2l_params(ctypes.Structure):
     _fields_ = [("g", _D), ("chi", _D), ("cfl", _D), ("eps", _D), ("eps_num", _D),
                 ("weno_gamma_hi", _D), ("weno_eps", _D), ("precision", ctypes.c_int32),
-                ("indicator", ctypes.c_int32), ("indicator_threshold", ctypes.c_float)]
+                ("indicator", ctypes.c_int32), ("indicator_threshold", ctypes.c_float),
+                ("staging_poll_limit", ctypes.c_int32)]
 
 
 class gks2l_stats_t(ctypes.Structure):
@@ -94,13 +107,17 @@ def load(path: str = LIB_PATH):
 
 
 class GKSError(RuntimeError):
-    pass
+    """A gks2l call returned a GKS2L_E* code (kept in .code)."""
+
+    def __init__(self, msg, code=0):
+        super().__init__(msg)
+        self.code = code
 
 
 def _check(rc, what):
     if rc != 0:
         msg = load().gks2l_error_string(rc).decode()
-        raise GKSError("%s failed: %s (%d)" % (what, msg, rc))
+        raise GKSError("%s failed: %s (%d)" % (what, msg, rc), rc)
 
 
 def _np_ptr(a):
@@ -270,7 +287,8 @@ class Solver:
 
 def cfl_mass_noalloc(avg, area, dX, g, cfl, out, stream=None):
     """gks2l_cfl_mass_noalloc on device tensors (float64, same cell order):
-    writes (dt, mass of layer 1, mass of layer 2) into `out` (3 doubles)."""
+    writes (dt, mass of layer 1, mass of layer 2, number of unusable cells)
+    into `out` (4 doubles)."""
     n = area.numel()
     s = _P(stream.cuda_stream) if stream is not None else None
     _check(load().gks2l_cfl_mass_noalloc(n, _P(avg.data_ptr()), _P(area.data_ptr()), _P(dX.data_ptr()),

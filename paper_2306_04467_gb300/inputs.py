@@ -412,6 +412,52 @@ def internal_wave_ridge(nx: int = 5656, ny: int = 707, seed: int = 2311, quad: i
     return Problem("internal_wave_ridge", mesh, bv, avg, grad, g=9.81, chi=0.97, cfl=0.5)
 
 
+def _two_states(mesh, inside, left, right, quad=8):
+    """Cell averages of a two-state layer split: (h1, h2) = left where
+    inside(x, y), right elsewhere (exact area fractions by quadrature), zero
+    velocity and gradients."""
+    frac = cell_average(lambda x, y: inside(x, y).astype(np.float64), mesh, quad)
+    avg = np.zeros((6, mesh.n_tri))
+    avg[3] = left[0] * frac + right[0] * (1.0 - frac)
+    avg[0] = left[1] * frac + right[1] * (1.0 - frac)
+    return avg, np.zeros((6, 2, mesh.n_tri))
+
+
+def riemann_one(n: int = 100, ny: int = 4, seed: int = 7) -> Problem:
+    """The paper's Riemann problem I (Sec. 4.3): (h1, h2) = (0.5, 0.5) left of
+    the jump and (0.55, 0.45) right of it, U = 2.5 in both layers, chi = 0.98,
+    G = 10, t = 0.1, on squares of side 1/n. A periodic strip [0, 3] x
+    [0, ny/n] stands in for the paper's [0, 1] x [0, 0.5]: the jump at x = 0.3
+    and a mirrored one at x = 1.8, whose waves cannot reach the first one's
+    region by t = 0.1."""
+    mesh = jittered_mesh(3 * n, ny, domain=(0.0, 3.0, 0.0, ny / n), seed=seed, bc="periodic")
+    avg, grad = _two_states(mesh, lambda x, y: (x >= 0.3) & (x < 1.8), (0.55, 0.45), (0.5, 0.5))
+    avg[4], avg[1] = 2.5 * avg[3], 2.5 * avg[0]
+    return Problem("riemann_one", mesh, np.zeros(mesh.n_vert), avg, grad, g=10.0, chi=0.98, cfl=0.5, t_end=0.1)
+
+
+def riemann_two(n: int = 40, seed: int = 8) -> Problem:
+    """The paper's Riemann problem II (Sec. 4.3): (h1, h2) = (0.2, 1.8) for
+    x < 5 and (1.8, 0.2) for x >= 5 on [0, 10] x [0, 1], zero velocity,
+    chi = 0.98, G = 9.81, t = 1, squares of side 1/n. Walls close the ends,
+    which no wave reaches by t = 1."""
+    mesh = jittered_mesh(10 * n, n, domain=(0.0, 10.0, 0.0, 1.0), seed=seed, bc="wall")
+    avg, grad = _two_states(mesh, lambda x, y: x < 5.0, (0.2, 1.8), (1.8, 0.2))
+    return Problem("riemann_two", mesh, np.zeros(mesh.n_vert), avg, grad, g=9.81, chi=0.98, cfl=0.5, t_end=1.0)
+
+
+def circular_interface(n: int = 10, seed: int = 9) -> Problem:
+    """The paper's 2-D interface propagation (Sec. 4.6): (h1, h2) = (1.8, 0.2)
+    inside the circle of radius 2 about (5, 5) and (0.2, 1.8) outside, on
+    [0, 10]^2, zero velocity, chi = 0.98, G = 9.81, run to t = 4, squares of
+    side 1/n. Walls stand in for the paper's free boundaries: the surface is
+    flat at the start and the interface's waves stay far from the sides."""
+    mesh = jittered_mesh(10 * n, 10 * n, domain=(0.0, 10.0, 0.0, 10.0), seed=seed, bc="wall")
+    avg, grad = _two_states(mesh, lambda x, y: (x - 5.0) ** 2 + (y - 5.0) ** 2 < 4.0, (1.8, 0.2), (0.2, 1.8))
+    return Problem("circular_interface", mesh, np.zeros(mesh.n_vert), avg, grad, g=9.81, chi=0.98, cfl=0.5,
+                   t_end=4.0)
+
+
 # ---------------------------------------------------------------------------
 # troubled-cell gate: seeded network parameters and synthetic samples
 # ---------------------------------------------------------------------------

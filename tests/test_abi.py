@@ -31,6 +31,20 @@ def test_binding_covers_the_header():
     assert set(declared_functions()) == set(gks2l.SIGNATURES)
 
 
+def test_binding_constants_match_the_header():
+    """Every GKS2L_ constant the header defines has the same value in the
+    binding, and the parameter struct has the header's fields in order."""
+    text = open(HEADER).read()
+    defs = dict(re.findall(r"#define (GKS2L_[A-Z0-9_]+)\s+(-?\d+)\s", text))
+    assert len(defs) >= 20
+    for name, val in defs.items():
+        assert getattr(gks2l, name) == int(val), name
+    body = re.search(r"typedef struct \{([^}]*)\} gks2l_params;", text).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(\w+)\s*[,;]", body)
+    assert fields == [f for f, _ in gks2l.gks2l_params._fields_]
+
+
 def test_host_only_calls_work_without_gpu():
     lib = gks2l.load()
     p = gks2l.default_params()

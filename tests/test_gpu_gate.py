@@ -295,20 +295,19 @@ def test_full_size_dambreak_with_gate(trained):
 
 def test_large_internal_wave(trained):
     """The large configuration: internal wave over a ridge on 7,997,584
-    triangles, FP32 + learned gate + FP64 balance terms, 500 stages. Both
-    layers keep their mass to rounding and the depths stay positive and
-    finite.
-
-    Not 2000 stages: at density ratios near 1 the method as read (the FP64
-    form and the oracle alike) carries a grid-scale mode that grows by a few
-    percent per stage at CFL 0.5 and ends the run near stage 1000 on any
-    mesh; at this resolution it already dominates the discharges by stage
-    500 (printed below), so only the invariants are checked."""
+    triangles, FP32 + learned gate + FP64 balance terms, all 2000 stages at
+    the paper's CFL 0.5. Both layers keep their mass to rounding, the depths
+    stay positive and the discharges stay at the internal wave's scale: the
+    linear wave of an interface depression a = 0.1 carries a layer discharge
+    of about c_i a h2 / (h1 + h2) = 0.0074 (c_i = sqrt((1 - chi) G h1 h2 /
+    (h1 + h2)) = 0.25), so |hu| <= 0.02 leaves room for the ridge's
+    amplification, and the flow across the channel, which only the mesh's
+    irregularity drives, stays below 0.01."""
     P, _ = trained
     prob = inputs.internal_wave_ridge()
     assert prob.mesh.n_tri == 7997584
     s = gated_solver(prob, P)
-    s.advance(500)
+    s.advance(2000)
     a, _ = s.get_state()
     st = s.stats()
     assert st["status"] == 0 and np.isfinite(a).all() and a[0].min() > 0 and a[3].min() > 0
@@ -316,5 +315,7 @@ def test_large_internal_wave(trained):
     for v in (0, 3):
         m0, m1 = area @ prob.avg[v], area @ a[v]
         assert abs(m1 - m0) <= 1e-12 * m0
-    print("large internal wave: t %.4f after 500 stages, smooth fraction %.3f, max |hu| %.3g"
-          % (st["t"], st["smooth_fraction"], np.abs(a[[1, 2, 4, 5]]).max()))
+    hu, hv = np.abs(a[[1, 4]]).max(), np.abs(a[[2, 5]]).max()
+    print("large internal wave: t %.4f after 2000 stages, smooth fraction %.3f, max |hu| %.3g, max |hv| %.3g"
+          % (st["t"], st["smooth_fraction"], hu, hv))
+    assert hu <= 0.02 and hv <= 0.01, (hu, hv)
