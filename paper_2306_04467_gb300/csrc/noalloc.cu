@@ -14,10 +14,10 @@ namespace {
 constexpr int kBlocks = 1024;      // partial results held in the scratch array
 constexpr int kThreads = 256;
 
-// 3 doubles per block: min(dX / U_max), sum |Omega| h1, sum |Omega| h2.
-// Every block of a call writes its slot before the final pass reads it, so
-// nothing has to start at zero.
-static __device__ __align__(256) double g_noalloc_scratch[3 * kBlocks];
+// 4 doubles per block: min(dX / U_max), sum |Omega| h1, sum |Omega| h2 and
+// the number of unusable cells. Every block of a call writes its slot before
+// the final pass reads it, so nothing has to start at zero.
+static __device__ __align__(256) double g_noalloc_scratch[4 * kBlocks];
 
 __device__ __forceinline__ double warp_min(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -28,68 +28,82 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// block-wide (min, sum, sum) of one value per thread; result in thread 0
-__device__ void block_reduce(double &r, double &m1, double &m2) {
-  __shared__ double sr[kThreads / 32], s1[kThreads / 32], s2[kThreads / 32];
+// block-wide (min, sum, sum, sum) of one value per thread; result in thread 0
+__device__ void block_reduce(double &r, double &m1, double &m2, double &nb) {
+  __shared__ double sr[kThreads / 32], s1[kThreads / 32], s2[kThreads / 32], sb[kThreads / 32];
   r = warp_min(r);
   m1 = warp_sum(m1);
   m2 = warp_sum(m2);
+  nb = warp_sum(nb);
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) { sr[w] = r; s1[w] = m1; s2[w] = m2; }
+  if (lane == 0) { sr[w] = r; s1[w] = m1; s2[w] = m2; sb[w] = nb; }
   __syncthreads();
   if (w == 0) {
     r = lane < kThreads / 32 ? sr[lane] : INFINITY;
     m1 = lane < kThreads / 32 ? s1[lane] : 0.0;
     m2 = lane < kThreads / 32 ? s2[lane] : 0.0;
+    nb = lane < kThreads / 32 ? sb[lane] : 0.0;
     r = warp_min(r);
     m1 = warp_sum(m1);
     m2 = warp_sum(m2);
+    nb = warp_sum(nb);
   }
 }
 
 // pass 1: per-block partials over a grid-stride range of cells
 __global__ void __launch_bounds__(kThreads) k_cfl_partial(int n, const double *avg, const double *area,
                                                          const double *dX, double g, double *scratch) {
-  double r = INFINITY, m1 = 0, m2 = 0;
+  double r = INFINITY, m1 = 0, m2 = 0, nbad = 0;
   for (int j = blockIdx.x * kThreads + threadIdx.x; j < n; j += gridDim.x * kThreads) {
     double um = 0;
+    bool bad = false;
     for (int l = 0; l < 2; l++) {
       // layer l: depth at variable 3 (lower) or 0 (upper)
       int b = l == 0 ? 3 : 0;
       double h = avg[(size_t)b * n + j];
       double u = avg[(size_t)(b + 1) * n + j] / h, v = avg[(size_t)(b + 2) * n + j] / h;
-      um = fmax(um, sqrt(u * u + v * v) + sqrt(g * h));
+      double sp = sqrt(u * u + v * v) + sqrt(g * h);
+      // a non-positive depth or a non-finite speed makes the cell unusable
+      // (fmax would otherwise drop a NaN speed)
+      bad = bad || !(h > 0) || !isfinite(sp);
+      um = fmax(um, sp);
     }
     double q = dX[j] / um;
-    r = fmin(r, (q > 0 && isfinite(q)) ? q : INFINITY);
+    bad = bad || !(q > 0 && isfinite(q));
+    r = fmin(r, bad ? INFINITY : q);
+    nbad += bad ? 1.0 : 0.0;
     m1 += area[j] * avg[(size_t)3 * n + j];
     m2 += area[j] * avg[j];
   }
-  block_reduce(r, m1, m2);
+  block_reduce(r, m1, m2, nbad);
   if (threadIdx.x == 0) {
-    scratch[3 * blockIdx.x] = r;
-    scratch[3 * blockIdx.x + 1] = m1;
-    scratch[3 * blockIdx.x + 2] = m2;
+    scratch[4 * blockIdx.x] = r;
+    scratch[4 * blockIdx.x + 1] = m1;
+    scratch[4 * blockIdx.x + 2] = m2;
+    scratch[4 * blockIdx.x + 3] = nbad;
   }
 }
 
-// pass 2: one block folds the partials and writes (dt, mass1, mass2)
+// pass 2: one block folds the partials and writes (dt, mass1, mass2, bad)
 __global__ void __launch_bounds__(kThreads) k_cfl_final(int nb, const double *scratch, double cfl, double *out) {
-  double r = INFINITY, m1 = 0, m2 = 0;
+  double r = INFINITY, m1 = 0, m2 = 0, nbad = 0;
   for (int b = threadIdx.x; b < nb; b += kThreads) {
-    r = fmin(r, scratch[3 * b]);
-    m1 += scratch[3 * b + 1];
-    m2 += scratch[3 * b + 2];
+    r = fmin(r, scratch[4 * b]);
+    m1 += scratch[4 * b + 1];
+    m2 += scratch[4 * b + 2];
+    nbad += scratch[4 * b + 3];
   }
-  block_reduce(r, m1, m2);
+  block_reduce(r, m1, m2, nbad);
   if (threadIdx.x == 0) {
     out[0] = cfl * r;
     out[1] = m1;
     out[2] = m2;
+    out[3] = nbad;
   }
 }
 
-// device address of the scratch array, looked up once per device
+// device address of the scratch array, looked up once per device (and kept:
+// a cudaDeviceReset would make it stale, which the header rules out)
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double *g_addr[kMaxDevices] = {nullptr};
