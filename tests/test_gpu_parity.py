@@ -48,7 +48,14 @@ def max_rel(prob, a, gr, ao, go):
 
 def run_both(prob, n_stages, t_end=0.0, precision=FP64):
     s = g.problem_solver(prob, precision=precision)
-    tg = s.advance(n_stages, t_end=t_end)
+    if t_end > 0:
+        # in chunks: gks2l_advance enqueues every stage it is asked for
+        done, tg = 0, 0.0
+        while done < n_stages and tg < t_end * (1 - 1e-12):
+            tg = s.advance(min(200, n_stages - done), t_end=t_end)
+            done += 200
+    else:
+        tg = s.advance(n_stages, t_end=t_end)
     a, gr = s.get_state()
     st = s.stats()
     o = Oracle.from_problem(prob)
