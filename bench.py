@@ -292,6 +292,7 @@ def run_profile_case(args):
     par = g.default_params(g=prob.g, chi=prob.chi, cfl=prob.cfl, precision=prec, **kw)
     s = g.Solver(prob.mesh, par, prob.b_vert)
     s.set_state(prob.avg, prob.grad)
+    s.set_launch_shapes([1, 1, 1, args.gate_variant])
     if kw:
         s.set_mlp(P)
         s.advance(2)   # the first stage after set_mlp is the plain method
@@ -302,6 +303,7 @@ def run_profile_case(args):
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     print(json.dumps({"profile_case": args.profile_case, "workload": args.workload, "form": args.form,
+                      "gate_variant": args.gate_variant,
                       "n_tri": prob.mesh.n_tri, "n_edges": n_edges(prob), "kernel_ms": ms}))
 
 
@@ -340,6 +342,9 @@ def main():
                     help="profiling mode: one step of the workload with this many squares across its short "
                          "side, kernels launched one by one (for ncu captures of a small case)")
     ap.add_argument("--form", default="fp32_learned", choices=["fp32", "fp32_learned", "fp64"])
+    ap.add_argument("--gate-variant", type=int, default=0, choices=[0, 1, 2],
+                    help="profiling mode: the gate kernel (0: mma.sync warp tiles, 1: tcgen05 CTA tiles, "
+                         "2: tcgen05 with twice the blocks per SM)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -419,10 +424,15 @@ def main():
                 reps = []
                 with sampler:
                     torch.cuda.synchronize(dev)
+                    if headline and form == "fp32_learned":
+                        # a profiler started with capture off records the timed region
+                        torch.cuda.profiler.start()
                     e0.record(stream)
                     s.advance(2 * k_form, sync=False)
                     e1.record(stream)
                     torch.cuda.synchronize(dev)
+                    if headline and form == "fp32_learned":
+                        torch.cuda.profiler.stop()
                     if headline and form == "fp32_learned":
                         # extra blocks of K steps, beside the value: the clock
                         # record covers them all (the state keeps advancing)

@@ -141,13 +141,23 @@ int gks2l_workspace_bytes(const gks2l_ctx *ctx, size_t *bytes);
  * the mesh operators. The library never frees the workspace. */
 int gks2l_bind(gks2l_ctx *ctx, void *d_workspace, size_t bytes, void *stream);
 
-/* Bottom B sampled at the vertices (host, n_vert doubles, concatenated over
- * instances for an ensemble); B is continuous and linear on each triangle.
- * May be called before or after gks2l_bind. */
+/* The bottom topography B of the source L^S1 (Sec. 3.2, Eq. SWE-semi-source:
+ * h_j (0, -G B_x, -G B_y)) and of the water level h1 + B (Sec. 3.2's
+ * well-balanced condition): the paper's "discretized bottom" (Sec. 4.2),
+ * read here as B sampled at the vertices (host, n_vert doubles, concatenated
+ * over instances for an ensemble), continuous and linear on each triangle.
+ * May be called before or after gks2l_bind; a state must be set again after
+ * it (GKS2L_ESTATE otherwise). */
 int gks2l_set_bathymetry(gks2l_ctx *ctx, const double *b_vert);
 
-/* Set the state from host arrays (avg: 6*n_tri, grad: 12*n_tri or NULL for
- * zero gradients) in the caller's order; resets time and step counters.
+/* Set the state: the cell averages W_j (Eq. SWE-cell-average) of the
+ * variables of Eq. SWE-macro, (h2, h2U2, h2V2, h1, h1U1, h1V1), and their
+ * cell-averaged gradients (the compact scheme's second set of unknowns,
+ * Sec. 3.3, Eq. slope), from host arrays (avg: 6*n_tri, grad: 12*n_tri or
+ * NULL for zero gradients) in the caller's order; resets time and step
+ * counters. A depth <= 0 or a non-finite value is reported in the status
+ * (GKS2L_ENEGDEPTH, GKS2L_ENONFINITE) that gks2l_stats and gks2l_advance
+ * return; setting a good state clears it.
  * Each instance's reference levels (the area-weighted means of h2 and
  * h1 + B, rounded to 2^-32, about which the FP32 form computes deviations)
  * are reduced on the device in a fixed order. Returns after the host arrays
@@ -160,17 +170,27 @@ int gks2l_set_state_device(gks2l_ctx *ctx, const double *d_avg, const double *d_
 
 /* Advance by up to n_stages stages (two stages make one S2O4 step). With
  * t_end > 0 each step is shortened to land on t_end and no step starts at or
- * after it. Enqueues work on the bound stream; t_out (if not NULL) forces a
- * synchronisation and returns the time of instance 0. Returns a device
- * status code only when t_out is requested. */
+ * after it; every 32 steps the call reads the instances' times back
+ * (synchronising the stream) and returns once all have reached t_end, so a
+ * large n_stages with an end time costs only the steps needed (plus at most
+ * 31). Without t_end it only enqueues work on the bound stream. t_out (if not
+ * NULL) forces a synchronisation and returns the time of instance 0. Returns
+ * a device status code only when t_out is requested. */
 int gks2l_advance(gks2l_ctx *ctx, int32_t n_stages, double t_end, double *t_out);
 
-/* Copy the state to host arrays (caller order); synchronises the stream. */
+/* Copy the state (the averages and cell-averaged gradients of Eq. SWE-macro's
+ * variables, as gks2l_set_state takes them) to host arrays (caller order);
+ * synchronises the stream. A state read out and set again continues bit for
+ * bit as if uninterrupted (plain forms; the gate restarts from the plain
+ * method). */
 int gks2l_get_state(gks2l_ctx *ctx, double *avg, double *grad);
 /* Copy the state to device arrays (caller order) on the bound stream. */
 int gks2l_get_state_device(gks2l_ctx *ctx, double *d_avg, double *d_grad);
 
-/* Mass sums, time, step and device status; synchronises the stream. */
+/* Statistics: each layer's mass sum_j |Omega_j| h_j (the quantity the
+ * finite-volume form Eq. SWE-semi-discrete conserves), the time and last
+ * step (Sec. 4's CFL step), the stages done and the device status;
+ * synchronises the stream. */
 int gks2l_stats(gks2l_ctx *ctx, gks2l_stats_t *out);
 
 /* ---- learned troubled-cell gate (not part of the paper) ------------------
@@ -233,16 +253,25 @@ int gks2l_mlp_forward(const float *d_X, int32_t n, const float *d_params, float 
  * shapes (with the gate on, the edge shape applies to the fused interface and
  * edge kernel): 0: 64 threads per block, 1: 128 (default), 2: 256, 3: 128 threads
  * held to 64 registers (eight blocks per SM), 4: 128 threads held to 128
- * registers (four blocks per SM). Results do not depend on them. */
+ * registers (four blocks per SM). shapes[3] picks the learned gate's kernel:
+ * 0 (default): each warp takes 32 cells through mma.sync BF16 tiles, the
+ * network in registers; 1: each 128-thread block takes 128 cells through
+ * tcgen05 MMAs (M = 128, N = 32) with the accumulators in tensor memory and
+ * the network in shared memory; 2: the same kernel with twice as many blocks
+ * per SM. The gate kernels may differ in the last bit of a logit. */
 #define GKS2L_LAUNCH_SHAPES 5
-int gks2l_set_launch_shapes(gks2l_ctx *ctx, const int32_t shapes[3]);
+#define GKS2L_GATE_VARIANTS 3
+int gks2l_set_launch_shapes(gks2l_ctx *ctx, const int32_t shapes[4]);
 
 /* Autotuner: advances the state by GKS2L_LAUNCH_SHAPES * n_steps full steps,
  * exactly as gks2l_advance would, timing the interface, edge and update
  * kernels in each shape (CUDA events on the bound stream); keeps the fastest
- * for each and writes them to shapes[3]. Requires a state and phase at a step
- * boundary; returns the run's status like gks2l_advance with t_out. */
-int gks2l_autotune(gks2l_ctx *ctx, int32_t n_steps, int32_t shapes[3]);
+ * for each. With the gate on it then times GKS2L_GATE_VARIANTS * (n_steps + 1)
+ * more steps, whole steps per gate kernel (the gate overlaps the edge
+ * kernels, so its own time does not decide), and keeps the faster. Writes the
+ * choices to shapes[4]. Requires a state and phase at a step boundary;
+ * returns the run's status like gks2l_advance with t_out. */
+int gks2l_autotune(gks2l_ctx *ctx, int32_t n_steps, int32_t shapes[4]);
 
 /* Kernel timing for roofline reports: advances n_steps full steps (exactly
  * like gks2l_advance, state included) but launches the stage kernels one by

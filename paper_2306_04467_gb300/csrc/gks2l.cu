@@ -27,6 +27,7 @@
 #include "mlp.cuh"
 #include "prep.h"
 #include "stage.cuh"
+#include "tcgen05.cuh"
 
 using namespace gks2l;
 
@@ -243,6 +244,130 @@ __global__ void __launch_bounds__(128) k_gate(Dev d, Par p) {
   }
 }
 
+// The same gate on the fifth-generation tensor cores: a CTA of 128 threads
+// takes 128 cells at a time, one per thread. Each thread writes its cell's
+// 24 features (BF16, normalisation folded into the first layer) as one row
+// of the A operand in shared memory; one thread issues the layer's MMAs
+// (M = 128, N = 32, K = 2 x 16, BF16 in, FP32 out) into tensor memory; each
+// warp reads its 32 rows back, adds the bias, applies ReLU and rounds to
+// BF16 (the next layer's A operand), and the output layer (N = 1) runs on
+// the FP32 pipes. The weights sit in shared memory, not registers. Waits on
+// the MMAs' completion are bounded: a wait that gives up records the
+// timeout, waits once more and the CTA frees its tensor memory and leaves.
+constexpr int GATE_TC_M = 128;
+constexpr unsigned GATE_TC_COLS = 32;   // tensor-memory columns: the 32 FP32 outputs of a layer
+struct GateTcSmem {
+  alignas(128) unsigned char x[GATE_TC_M * 64];   // [128][32] BF16 features, operand layout
+  alignas(128) unsigned char h[GATE_TC_M * 64];   // [128][32] BF16 layer-1 activations
+  alignas(128) unsigned char w1[32 * 64];         // [32 out][32 in] BF16
+  alignas(128) unsigned char w2[32 * 64];
+  float b1[32], b2[32], w3[32];
+  float b3, threshold;
+  alignas(8) unsigned long long bar;
+  uint32_t tmem;
+};
+
+__device__ __forceinline__ uint4 pack8_bf16(const float *v) {
+  uint4 r;
+  r.x = pack_bf16(v[0], v[1]);
+  r.y = pack_bf16(v[2], v[3]);
+  r.z = pack_bf16(v[4], v[5]);
+  r.w = pack_bf16(v[6], v[7]);
+  return r;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(GATE_TC_M) k_gate_tc(Dev d, Par p) {
+  __shared__ GateTcSmem S;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const MlpDev &w = *reinterpret_cast<const MlpDev *>(d.mlp);
+  for (int i = tid; i < 32 * 32; i += GATE_TC_M) {
+    const int n = i >> 5, k = i & 31;
+    *reinterpret_cast<__nv_bfloat16 *>(S.w1 + tc::tile_offset(n, k)) = w.w1[i];
+    *reinterpret_cast<__nv_bfloat16 *>(S.w2 + tc::tile_offset(n, k)) = w.w2[i];
+  }
+  if (tid < 32) {
+    S.b1[tid] = w.b1[tid];
+    S.b2[tid] = w.b2[tid];
+    S.w3[tid] = w.w3[tid];
+  }
+  if (tid == 0) {
+    S.b3 = w.b3;
+    S.threshold = w.threshold;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tc::alloc(&S.tmem, GATE_TC_COLS);
+  tc::fence_proxy();        // the weight tiles, for the tensor cores
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = S.tmem, twarp = tbase + ((uint32_t)(warp * 32) << 16);
+  const uint32_t idesc = tc::idesc_bf16(GATE_TC_M, 32);
+  const unsigned ax = smem_addr(S.x), ah = smem_addr(S.h), a1 = smem_addr(S.w1), a2 = smem_addr(S.w2);
+  const int ntile = (d.nt + GATE_TC_M - 1) / GATE_TC_M, nword = (d.nt + TW - 1) / TW;
+  unsigned phase = 0;
+  bool failed = false;
+  for (int tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
+    const int j = tile * GATE_TC_M + tid;
+    const bool active = j < d.nt && (p.all_active || d.dt[d.inst[j]] > 0);
+    float f[32];
+    if (active) gate_features<R>(d, j, d.st_cell, d.st_xf, d.cs, j, f);
+    else
+      for (int k = 0; k < 24; k++) f[k] = 0.f;
+    for (int k = 24; k < 32; k++) f[k] = 0.f;
+    for (int c = 0; c < 4; c++) *reinterpret_cast<uint4 *>(S.x + tc::tile_offset(tid, 8 * c)) = pack8_bf16(f + 8 * c);
+    float z[32], logit = 0.f;
+    for (int layer = 0; layer < 2 && !failed; layer++) {
+      tc::fence_proxy();
+      tc::fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after();
+        const unsigned a = layer == 0 ? ax : ah, b = layer == 0 ? a1 : a2;
+        tc::mma_bf16(tbase, tc::smem_desc(a), tc::smem_desc(b), idesc, 0);
+        tc::mma_bf16(tbase, tc::smem_desc(a + 2 * tc::kLbo), tc::smem_desc(b + 2 * tc::kLbo), idesc, 1);
+        tc::commit(&S.bar);
+      }
+      const bool done = mbar_wait_bounded(&S.bar, phase, 1000000000ull);
+      if (!__syncthreads_and(done)) {
+        // record, wait once more so no MMA outlives the tensor memory, leave
+        if (tid == 0) atomicOr(d.status, ST_TIMEOUT);
+        if (!done && !mbar_wait_bounded(&S.bar, phase, 1000000000ull)) atomicOr(d.status, ST_COPY_LOST);
+        failed = true;
+        break;
+      }
+      phase ^= 1u;
+      tc::fence_after();
+      tc::ld32(twarp, z);
+      if (layer == 0) {
+        for (int k = 0; k < 32; k++) z[k] = fmaxf(z[k] + S.b1[k], 0.f);
+        for (int c = 0; c < 4; c++)
+          *reinterpret_cast<uint4 *>(S.h + tc::tile_offset(tid, 8 * c)) = pack8_bf16(z + 8 * c);
+      } else {
+        // activations rounded to BF16 like the operands of the tensor-core layers
+        float s0 = 0.f, s1 = 0.f;
+        for (int k = 0; k < 32; k += 2) {
+          s0 += __bfloat162float(__float2bfloat16_rn(fmaxf(z[k] + S.b2[k], 0.f))) * S.w3[k];
+          s1 += __bfloat162float(__float2bfloat16_rn(fmaxf(z[k + 1] + S.b2[k + 1], 0.f))) * S.w3[k + 1];
+        }
+        logit = s0 + s1 + S.b3;
+      }
+    }
+    if (failed) break;
+    const bool smooth = active && logit < S.threshold;
+    const unsigned mask = __ballot_sync(FULL, smooth || !active);
+    const int word = tile * (GATE_TC_M / TW) + warp;
+    if (lane == 0 && word < nword) d.gate_mask[word] = mask;
+    if (p.logit_out && j < d.nt) p.logit_out[j] = logit;
+    tc::fence_before();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0) tc::dealloc(tbase, GATE_TC_COLS);
+}
+
 // gate network image for the reconstruction blocks (one block)
 __global__ void k_mlp_pack(const float *P, float threshold_logit, MlpDev *out) {
   mlp_pack_folded(*out, P, threshold_logit, threadIdx.x, blockDim.x);
@@ -315,7 +440,7 @@ __device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage)
   // its instance's dt is known, so the unit's loads issue at once; only
   // edges of instances still running are written
   R out[12], own[2];
-  edge_unit<R>(d, p, ee, ell, q, stage, out, nullptr, own);
+  edge_unit<R, false, true>(d, p, ee, ell, q, stage, out, nullptr, own);
   const bool ok = e < d.ne && d.dt[d.inst[d.eL[ee]]] > 0;
   own_write<R>(d, e, ell, q, own, ok);
   // the Gauss point q = 0 thread averages the fluxes (out[0..5]), the q = 1
@@ -341,7 +466,7 @@ __device__ __forceinline__ void edge_fused_body(const Dev &d, const Par &p, int 
   int e = tid >> 2, ell = (tid >> 1) & 1, q = tid & 1;
   const int ee = e < d.ne ? e : d.ne - 1;
   R out[12], bl = 0, own[2];
-  const bool done = edge_unit<R, true>(d, p, ee, ell, q, stage, out, &bl, own);
+  const bool done = edge_unit<R, true, true>(d, p, ee, ell, q, stage, out, &bl, own);
   if (!done) {
     for (int k = 0; k < 12; k++) out[k] = 0;
   }
@@ -701,7 +826,7 @@ struct gks2l_ctx {
   bool has_mlp = false;
   int n_sm = 1;                // SMs of the bound device
   cudaStream_t side = nullptr; // second stream for the gate (created with the network)
-  int shape[3] = {1, 1, 1};    // launch shapes of the interface, edge and update kernels
+  int shape[4] = {1, 1, 1, 0}; // launch shapes of the interface, edge and update kernels; gate variant
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int phase = 0;
   int64_t stages = 0;
@@ -894,10 +1019,16 @@ Par make_par(const gks2l_ctx *c) {
 }
 
 
+// the gate in its chosen variant: 0: warp tiles of 32 cells on mma.sync,
+// 1: CTA tiles of 128 cells on tcgen05 with tensor-memory accumulators,
+// 2: the same with twice the CTAs per SM (more gathers in flight, more
+// overlap with the edge kernels)
 template <typename R>
 void launch_gate(gks2l_ctx *c, const Par &p, cudaStream_t st) {
-  const unsigned nb = std::min(blocks(c->d.nt, 4 * TW), (unsigned)(c->n_sm * GATE_BLOCKS_PER_SM));
-  k_gate<R><<<nb, 128, 0, st>>>(c->d, p);
+  const unsigned per_sm = c->shape[3] == 2 ? 2 * GATE_BLOCKS_PER_SM : GATE_BLOCKS_PER_SM;
+  const unsigned nb = std::min(blocks(c->d.nt, 4 * TW), (unsigned)(c->n_sm * per_sm));
+  if (c->shape[3] >= 1) k_gate_tc<R><<<nb, GATE_TC_M, 0, st>>>(c->d, p);
+  else k_gate<R><<<nb, 128, 0, st>>>(c->d, p);
 }
 
 template <typename R>
@@ -910,6 +1041,7 @@ void launch_recon(gks2l_ctx *c, const Par &p) {
 // 2: 256 threads (registers as the compiler likes), 3: 128 threads held to
 // 64 registers (eight blocks per SM), 4: 128 threads held to 128 registers
 constexpr int kShapes = 5;
+constexpr int kGateVariants = 3;   // gate kernel: 0 mma.sync warp tiles, 1 and 2 tcgen05 CTA tiles
 
 #define GKS2L_SHAPE_SWITCH(cfg, KERNEL, n, st, ...)                                          \
   switch (cfg) {                                                                           \
@@ -1227,6 +1359,8 @@ int gks2l_set_state_device(gks2l_ctx *c, const double *d_avg, const double *d_gr
   return after_state(c, d_grad);
 }
 
+constexpr int kAdvanceCheck = 32;   // steps between end-time checks in gks2l_advance
+
 int gks2l_advance(gks2l_ctx *c, int32_t n_stages, double t_end, double *t_out) {
   if (!c || n_stages < 0) return GKS2L_EINVAL;
   if (!c->bound || !c->has_state) return GKS2L_ESTATE;
@@ -1239,9 +1373,15 @@ int gks2l_advance(gks2l_ctx *c, int32_t n_stages, double t_end, double *t_out) {
     c->stages++;
   }
   int steps = left / 2;
+  bool arrived = false;
   if (steps > 0) {
     int rc = ensure_graph(c);
     if (rc) return rc;
+    // with an end time, every kAdvanceCheck steps the instances' times are
+    // read back and the call stops once all have reached it (later steps
+    // would change nothing)
+    std::vector<double> tv(t_end > 0 ? c->prep.ninst : 0);
+    const double tol = 1e-12 * std::max(1.0, std::fabs(t_end));
     for (int s = 0; s < steps; s++) {
       if (c->gexec) {
         CK(cudaGraphLaunch(c->gexec, c->stream));
@@ -1250,10 +1390,18 @@ int gks2l_advance(gks2l_ctx *c, int32_t n_stages, double t_end, double *t_out) {
         launch_stage_any(c, 1);
         launch_stage_any(c, 2);
       }
+      c->stages += 2;
+      if (t_end > 0 && (s + 1) % kAdvanceCheck == 0 && s + 1 < steps) {
+        CK(cudaMemcpyAsync(tv.data(), c->d.t, tv.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        arrived = true;
+        for (double t : tv)
+          if (t_end - t > tol) arrived = false;
+        if (arrived) break;
+      }
     }
-    c->stages += 2 * steps;
   }
-  if (left % 2) {
+  if (left % 2 && !arrived) {
     launch_step_begin(c);
     launch_stage_any(c, 1);
     c->phase = 1;
@@ -1400,16 +1548,17 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[6]) {
   return GKS2L_OK;
 }
 
-int gks2l_set_launch_shapes(gks2l_ctx *c, const int32_t shapes[3]) {
+int gks2l_set_launch_shapes(gks2l_ctx *c, const int32_t shapes[4]) {
   if (!c || !shapes) return GKS2L_EINVAL;
   for (int k = 0; k < 3; k++)
     if (shapes[k] < 0 || shapes[k] >= kShapes) return GKS2L_EINVAL;
-  for (int k = 0; k < 3; k++) c->shape[k] = shapes[k];
+  if (shapes[3] < 0 || shapes[3] >= kGateVariants) return GKS2L_EINVAL;
+  for (int k = 0; k < 4; k++) c->shape[k] = shapes[k];
   drop_graph(c);
   return GKS2L_OK;
 }
 
-int gks2l_autotune(gks2l_ctx *c, int32_t n_steps, int32_t shapes[3]) {
+int gks2l_autotune(gks2l_ctx *c, int32_t n_steps, int32_t shapes[4]) {
   if (!c || !shapes || n_steps <= 0) return GKS2L_EINVAL;
   if (!c->bound || !c->has_state || c->phase != 0) return GKS2L_ESTATE;
   double best[3] = {INFINITY, INFINITY, INFINITY};
@@ -1428,6 +1577,39 @@ int gks2l_autotune(gks2l_ctx *c, int32_t n_steps, int32_t shapes[3]) {
   }
   for (int k = 0; k < 3; k++) c->shape[k] = shapes[k] = pick[k];
   drop_graph(c);
+  // the gate runs beside the edge kernels on a second stream, so its variant
+  // is chosen by whole steps (captured graphs, CUDA events), not by its own time
+  shapes[3] = c->shape[3];
+  if (c->par.indicator == GKS2L_INDICATOR_MLP && c->has_mlp) {
+    double best_g = INFINITY;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double zero = 0.0;
+    CK(cudaMemcpyAsync(c->d_tend, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    for (int v = 0; v < kGateVariants; v++) {
+      c->shape[3] = v;
+      drop_graph(c);
+      int rc = ensure_graph(c);
+      if (rc) return rc;
+      CK(cudaGraphLaunch(c->gexec, c->stream));   // the first step after a switch, untimed
+      CK(cudaEventRecord(e0, c->stream));
+      for (int s = 0; s < n_steps; s++) CK(cudaGraphLaunch(c->gexec, c->stream));
+      CK(cudaEventRecord(e1, c->stream));
+      CK(cudaEventSynchronize(e1));
+      float t;
+      CK(cudaEventElapsedTime(&t, e0, e1));
+      c->stages += 2 * (n_steps + 1);
+      if (t < best_g) {
+        best_g = t;
+        shapes[3] = v;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->shape[3] = shapes[3];
+    drop_graph(c);
+  }
   return check_status(c);
 }
 

@@ -121,9 +121,24 @@ template <typename R> __host__ __device__ __forceinline__ R pv(double d, float f
 template <> __host__ __device__ __forceinline__ double pv<double>(double d, float) { return d; }
 template <> __host__ __device__ __forceinline__ float pv<float>(double, float f) { return f; }
 
-template <typename R> __host__ __device__ __forceinline__ R r_erf(R x);
-template <> __host__ __device__ __forceinline__ double r_erf<double>(double x) { return erf(x); }
-template <> __host__ __device__ __forceinline__ float r_erf<float>(float x) { return erff(x); }
+// erf(x) given ex = e^{-x^2}, which the caller has formed already: in FP64
+// the library erf; in FP32 the rational approximation 7.1.26 of Abramowitz
+// and Stegun (Handbook of Mathematical Functions, after Hastings), erf(|x|) =
+// 1 - (a1 t + ... + a5 t^5) e^{-x^2}, t = 1/(1 + p |x|), absolute error at most
+// 1.5e-7 (near FP32 rounding), one reciprocal and five multiply-adds
+template <typename R> __host__ __device__ __forceinline__ R erf_ex(R x, R ex);
+template <> __host__ __device__ __forceinline__ double erf_ex<double>(double x, double) { return erf(x); }
+template <> __host__ __device__ __forceinline__ float erf_ex<float>(float x, float ex) {
+  const float ax = x < 0.f ? -x : x;
+  const float t = 1.f / (1.f + 0.3275911f * ax);
+  float q = 1.061405429f;
+  q = q * t - 1.453152027f;
+  q = q * t + 1.421413741f;
+  q = q * t - 0.284496736f;
+  q = q * t + 0.254829592f;
+  const float e = 1.f - q * t * ex;
+  return x < 0.f ? -e : e;
+}
 template <typename R> __host__ __device__ __forceinline__ R r_erfc(R x);
 template <> __host__ __device__ __forceinline__ double r_erfc<double>(double x) { return erfc(x); }
 template <> __host__ __device__ __forceinline__ float r_erfc<float>(float x) { return erfcf(x); }
@@ -401,26 +416,99 @@ template <> __device__ __forceinline__ void load_rec<double, 12>(const double *p
 }
 #endif
 
-// R: the records' precision; T: the values' type (R, or a pair of points)
-template <typename R, typename T = R>
-__host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, T x, T y, T href, SideVals<T> &s) {
+// Operations rounded as written, whatever the compiler does with the code
+// around them: where two kernels must form the same value bit for bit.
+template <typename R> struct Rn;
+template <> struct Rn<float> {
+#ifdef __CUDA_ARCH__
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+#else
+  static float mul(float a, float b) { return a * b; }
+  static float add(float a, float b) { return a + b; }
+  static float sub(float a, float b) { return a - b; }
+  static float fma(float a, float b, float c) { return std::fma(a, b, c); }
+  static float rcp(float a) { return 1.0f / a; }
+#endif
+};
+template <> struct Rn<double> {
+#ifdef __CUDA_ARCH__
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+  static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
+#else
+  static double mul(double a, double b) { return a * b; }
+  static double add(double a, double b) { return a + b; }
+  static double sub(double a, double b) { return a - b; }
+  static double fma(double a, double b, double c) { return std::fma(a, b, c); }
+  static double rcp(double a) { return 1.0 / a; }
+#endif
+};
+
+// gradient (scaled by ih) of the level polynomial cf at a point's monomial
+// derivatives, explicitly rounded: the edge kernels take the other layer's
+// level gradient from the lane that formed it as its own, the deferred edge
+// pass forms it again, and both get the same bits
+template <typename R>
+__host__ __device__ __forceinline__ void level_grad(const R *cf, const R mx[10], const R my[10], R ih, R g[2]) {
+  using O = Rn<R>;
+  R ax = cf[1], ay = cf[2];
+  for (int k : {3, 4, 6, 7, 8}) ax = O::fma(cf[k], mx[k], ax);
+  for (int k : {4, 5, 7, 8, 9}) ay = O::fma(cf[k], my[k], ay);
+  g[0] = O::mul(ax, ih);
+  g[1] = O::mul(ay, ih);
+}
+// 2x2 rotation, explicitly rounded (for the level gradients above)
+template <typename R>
+__host__ __device__ __forceinline__ void rot2_rn(const double *M, R v[2]) {
+  using O = Rn<R>;
+  const R a = v[0], b = v[1];
+  v[0] = O::fma((R)M[1], b, O::mul((R)M[0], a));
+  v[1] = O::fma((R)M[3], b, O::mul((R)M[2], a));
+}
+
+// One side of an edge point: cell c's reconstruction of layer ell at scaled
+// point (x, y), seen through transform xf; href is the depth of the
+// reference level at the point. OTHER: also form the gradient of the other
+// layer's level from its record (otherwise the caller takes it from the lane
+// that forms it as its own).
+template <typename R, bool OTHER = true>
+__host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, R x, R y, R href, SideVals<R> &s) {
   const int N = d.cs;
-  R w[NREC], wo[12];
+  R w[NREC];
   load_rec<R, NREC>((const R *)d.srec + ((size_t)ell * N + c) * NREC, w);
-  load_rec<R, 12>((const R *)d.srec + ((size_t)(1 - ell) * N + c) * NREC, wo);
-  T m[10], mx[10], my[10];
-  monos<T>(x, y, m, mx, my);
+  R m[10], mx[10], my[10];
+  monos<R>(x, y, m, mx, my);
   const R ih = w[11];
-  T dev[3], gx[4], gy[4];
-  for (int i = 0; i < 4; i++) {
-    const R *cf = i < 3 ? w + 12 * i : wo;
-    T a = cf[0] * m[0], ax = cf[1] * mx[1], ay = cf[2] * my[2];
+  R dev[3], gx[3], gy[3];
+  for (int i = 0; i < 3; i++) {
+    const R *cf = w + 12 * i;
+    R a = cf[0] * m[0];
     for (int k = 1; k < 10; k++) a += cf[k] * m[k];
-    for (int k : {3, 4, 6, 7, 8}) ax += cf[k] * mx[k];
-    for (int k : {4, 5, 7, 8, 9}) ay += cf[k] * my[k];
-    if (i < 3) dev[i] = a;
-    gx[i] = ax * ih;
-    gy[i] = ay * ih;
+    dev[i] = a;
+    if (i == 0) {
+      R g[2];
+      level_grad<R>(cf, mx, my, ih, g);
+      gx[0] = g[0];
+      gy[0] = g[1];
+    } else {
+      R ax = cf[1] * mx[1], ay = cf[2] * my[2];
+      for (int k : {3, 4, 6, 7, 8}) ax += cf[k] * mx[k];
+      for (int k : {4, 5, 7, 8, 9}) ay += cf[k] * my[k];
+      gx[i] = ax * ih;
+      gy[i] = ay * ih;
+    }
+  }
+  s.goth[0] = s.goth[1] = 0;
+  if (OTHER) {
+    R wo[12];
+    load_rec<R, 12>((const R *)d.srec + ((size_t)(1 - ell) * N + c) * NREC, wo);
+    level_grad<R>(wo, mx, my, ih, s.goth);
   }
   s.d = w[10] + dev[0];
   s.h = href + s.d;
@@ -429,21 +517,20 @@ __host__ __device__ inline void side_vals(const Dev &d, int ell, int c, int xf, 
   s.glev[0] = gx[0]; s.glev[1] = gy[0];
   s.gm[0][0] = gx[1]; s.gm[0][1] = gy[1];
   s.gm[1][0] = gx[2]; s.gm[1][1] = gy[2];
-  s.goth[0] = gx[3]; s.goth[1] = gy[3];
   R gb[2] = {0, 0};
   if (ell == 0) { gb[0] = w[23]; gb[1] = w[35]; }
   if (xf != 0) {
     const double *M = d.xf + 4 * xf;
-    T mv[2] = {s.mx, s.my};
-    rot2<T>(M, mv);
+    R mv[2] = {s.mx, s.my};
+    rot2<R>(M, mv);
     s.mx = mv[0]; s.my = mv[1];
-    rot2<T>(M, s.glev);
-    rot2<T>(M, s.goth);
+    rot2_rn<R>(M, s.glev);
+    if (OTHER) rot2_rn<R>(M, s.goth);
     rot2<R>(M, gb);
-    T G2[2][2] = {{s.gm[0][0], s.gm[0][1]}, {s.gm[1][0], s.gm[1][1]}};
+    R G2[2][2] = {{s.gm[0][0], s.gm[0][1]}, {s.gm[1][0], s.gm[1][1]}};
     for (int i2 = 0; i2 < 2; i2++)
       for (int k = 0; k < 2; k++) {
-        T acc = (R)M[2 * i2] * G2[0][0] * (R)M[2 * k] + (R)M[2 * i2] * G2[0][1] * (R)M[2 * k + 1];
+        R acc = (R)M[2 * i2] * G2[0][0] * (R)M[2 * k] + (R)M[2 * i2] * G2[0][1] * (R)M[2 * k + 1];
         acc += (R)M[2 * i2 + 1] * G2[1][0] * (R)M[2 * k];
         acc += (R)M[2 * i2 + 1] * G2[1][1] * (R)M[2 * k + 1];
         s.gm[i2][k] = acc;
@@ -480,12 +567,12 @@ template <typename R> struct Kern {
 };
 
 // Central moments mu_k = <c^k> (k = 0..5, c = u - U) of the normalised 1-D
-// Maxwellian over the half line sgn*u > 0; e0 = mu_0 - 1/2, E = e^{-lam U^2}/(2 sqrt(pi lam)).
+// Maxwellian over the half line sgn*u > 0, from E = e^{-lam U^2}/(2 sqrt(pi lam))
+// (formed by the caller); e0 = mu_0 - 1/2.
 template <typename R>
-__host__ __device__ __forceinline__ void half_moments(R U, R lam, R sgn, R mu[6], R &e0, R &E) {
+__host__ __device__ __forceinline__ void half_moments_E(R U, R lam, R sgn, R E, R ex, R mu[6], R &e0) {
   const R th = (R)0.5 / lam;
-  e0 = sgn * (R)0.5 * r_erf<R>(r_sqrt<R>(lam) * U);
-  E = r_exp<R>(-lam * U * U) * (R)0.5 / r_sqrt<R>((R)3.14159265358979323846 * lam);
+  e0 = sgn * (R)0.5 * erf_ex<R>(r_sqrt<R>(lam) * U, ex);   // ex = e^{-lam U^2}
   mu[0] = (R)0.5 + e0;
   mu[1] = sgn * E;
   R pw = -sgn * U * E;
@@ -503,8 +590,9 @@ __host__ __device__ __forceinline__ void half_moments(R U, R lam, R sgn, R mu[6]
 template <typename R>
 __host__ __device__ __forceinline__ void half_moments_pm(R U, R lam, R mp[6], R mm[6]) {
   const R th = (R)0.5 / lam;
-  const R e0 = (R)0.5 * r_erf<R>(r_sqrt<R>(lam) * U);
-  const R E = r_exp<R>(-lam * U * U) * (R)0.5 / r_sqrt<R>((R)3.14159265358979323846 * lam);
+  const R ex = r_exp<R>(-lam * U * U);
+  const R e0 = (R)0.5 * erf_ex<R>(r_sqrt<R>(lam) * U, ex);
+  const R E = ex * (R)0.5 / r_sqrt<R>((R)3.14159265358979323846 * lam);
   for (int sg = 0; sg < 2; sg++) {
     const R sgn = sg == 0 ? (R)1 : (R)-1;
     R *mu = sg == 0 ? mp : mm;
@@ -594,18 +682,22 @@ __host__ __device__ inline void gks_layer(R href, R dl, R dr, R Ul, R Vl, R Ur, 
   const R dlr = dl - dr;                          // h_l - h_r, exact at rest
   const R laml = 1 / (g * hlR), lamr = 1 / (g * hrR);
   const R thl = (R)0.5 * g * hlR, thr = (R)0.5 * g * hrR;
-  R mul[6], mur[6], e0l, e0r, El, Er;
-  half_moments<R>(Ul, laml, (R)1, mul, e0l, El);
-  half_moments<R>(Ur, lamr, (R)-1, mur, e0r, Er);
+  // E = e^{-lam U^2} / (2 sqrt(pi lam)) = sqrt(G/(4 pi)) sqrt(h) e^{-lam U^2}
+  // on each side: one exponential and one square root serve the half-space
+  // moments and the depth-difference term below
+  const R xl = r_exp<R>(-laml * Ul * Ul), xr = r_exp<R>(-lamr * Ur * Ur);
+  const R sl = r_sqrt<R>(hlR), sr = r_sqrt<R>(hrR);
+  const R cphi = r_sqrt<R>(g * (R)(0.25 / 3.14159265358979323846));
+  const R El = cphi * sl * xl, Er = cphi * sr * xr;
+  R mul[6], mur[6], e0l, e0r;
+  half_moments_E<R>(Ul, laml, (R)1, El, xl, mul, e0l);
+  half_moments_E<R>(Ur, lamr, (R)-1, Er, xr, mur, e0r);
   // W-bar: the t = 0 interface state; h_b = (h_l + h_r)/2, h-bar = h_b + hdev
   const R db = (R)0.5 * (dl + dr);                // h_b - href
   const R hb = href + db;
   const R hdev = hlR * e0l + hrR * e0r;
   // h_l E_l - h_r E_r with h E = sqrt(G/(4 pi)) h^{3/2} e^{-lam U^2}, written
   // through h_l - h_r so that it vanishes exactly for equal depths and velocities
-  const R xl = r_exp<R>(-laml * Ul * Ul), xr = r_exp<R>(-lamr * Ur * Ur);
-  const R sl = r_sqrt<R>(hlR), sr = r_sqrt<R>(hrR);
-  const R cphi = r_sqrt<R>(g * (R)(0.25 / 3.14159265358979323846));
   const R dphi = dlr * (hlR + sl * sr + hrR) / (sl + sr);
   const R ediff = cphi * (hlR * sl * (xl - xr) + dphi * xr);
   const R mbn = (hlR * Ul * mul[0] + hrR * Ur * mur[0]) + ediff;
@@ -686,37 +778,6 @@ __host__ __device__ inline void gks_layer(R href, R dl, R dr, R Ul, R Vl, R Ur, 
 // with explicitly rounded operations so that the interface kernel and the
 // fused edge kernel, which both form it, get the same value whatever the
 // compiler does with the code around it.
-template <typename R> struct Rn;
-template <> struct Rn<float> {
-#ifdef __CUDA_ARCH__
-  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
-  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-  static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
-#else
-  static float mul(float a, float b) { return a * b; }
-  static float add(float a, float b) { return a + b; }
-  static float sub(float a, float b) { return a - b; }
-  static float fma(float a, float b, float c) { return std::fma(a, b, c); }
-  static float rcp(float a) { return 1.0f / a; }
-#endif
-};
-template <> struct Rn<double> {
-#ifdef __CUDA_ARCH__
-  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
-  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-  static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
-#else
-  static double mul(double a, double b) { return a * b; }
-  static double add(double a, double b) { return a + b; }
-  static double sub(double a, double b) { return a - b; }
-  static double fma(double a, double b, double c) { return std::fma(a, b, c); }
-  static double rcp(double a) { return 1.0 / a; }
-#endif
-};
 template <typename R>
 __host__ __device__ __forceinline__ R blend_level(R dl, R hl, R mxl, R myl, R dr, R hr, R mxr, R myr, R n0, R n1) {
   using O = Rn<R>;
@@ -788,7 +849,10 @@ __host__ __device__ __forceinline__ void plane_grad(const Dev &d, int c, int whi
 // every blended level of both cells, carry no weight; elsewhere it returns
 // false and the solution is left to a later pass (plain mode, plane
 // gradients gathered).
-template <typename R, bool FUSED = false>
+// PAIRED (the edge kernels' thread layout, where the lane two over holds the
+// same point and side for the other layer): the other layer's level
+// gradient comes from that lane by a shuffle instead of from its record.
+template <typename R, bool FUSED = false, bool PAIRED = false>
 __host__ __device__ inline bool edge_unit(const Dev &d, const Par &p, int e, int ell, int q, int stage, R out[12],
                                           R *blend = nullptr, R *own = nullptr) {
   const int NE = d.ne;
@@ -802,8 +866,19 @@ __host__ __device__ inline bool edge_unit(const Dev &d, const Par &p, int e, int
   (void)stage;
   const R href = ref_depth<R>(d, ell, e, q);
   SideVals<R> s[2];
-  side_vals<R>(d, ell, cL, 0, xl[(2 * q) * NE + e], xl[(2 * q + 1) * NE + e], href, s[0]);
-  side_vals<R>(d, ell, cR, xf, xr[(2 * q) * NE + e], xr[(2 * q + 1) * NE + e], href, s[1]);
+#ifdef __CUDA_ARCH__
+  constexpr bool SH = PAIRED;
+#else
+  constexpr bool SH = false;
+#endif
+  side_vals<R, !SH>(d, ell, cL, 0, xl[(2 * q) * NE + e], xl[(2 * q + 1) * NE + e], href, s[0]);
+  side_vals<R, !SH>(d, ell, cR, xf, xr[(2 * q) * NE + e], xr[(2 * q + 1) * NE + e], href, s[1]);
+#ifdef __CUDA_ARCH__
+  if (SH) {
+    for (int sd = 0; sd < 2; sd++)
+      for (int k = 0; k < 2; k++) s[sd].goth[k] = __shfl_xor_sync(0xffffffffu, s[sd].glev[k], 2);
+  }
+#endif
   // blended derivative of the other layer's level and the well-balance vector
   // D = grad h - grad Phi / G = grad(level) + c (w grad(other) + (1 - w) grad P1)
   const int oth = 1 - ell;  // hc / omg index of the other layer: 0 = eta1, 1 = h2

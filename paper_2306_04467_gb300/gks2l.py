@@ -36,6 +36,7 @@ GKS2L_ENOTIMPL = -8
 GKS2L_ETOOBIG = -9
 GKS2L_ETIMEOUT = -10
 GKS2L_LAUNCH_SHAPES = 5
+GKS2L_GATE_VARIANTS = 3
 
 # every entry point the header declares, with (restype, argtypes)
 _P = ctypes.c_void_p
@@ -75,8 +76,8 @@ SIGNATURES = {
     "gks2l_get_state_device": (_I, [_P, _P, _P]),
     "gks2l_stats": (_I, [_P, ctypes.POINTER(gks2l_stats_t)]),
     "gks2l_profile_kernels": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double * 6)]),
-    "gks2l_set_launch_shapes": (_I, [_P, ctypes.POINTER(ctypes.c_int32 * 3)]),
-    "gks2l_autotune": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32 * 3)]),
+    "gks2l_set_launch_shapes": (_I, [_P, ctypes.POINTER(ctypes.c_int32 * 4)]),
+    "gks2l_autotune": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32 * 4)]),
     "gks2l_alu_peaks": (_I, [_P, ctypes.POINTER(ctypes.c_double * 2)]),
     "gks2l_set_mlp": (_I, [_P, _P, ctypes.c_size_t]),
     "gks2l_harvest": (_I, [_P, ctypes.c_float, _P, _P, _P]),
@@ -169,6 +170,7 @@ class Solver:
             rc = L.gks2l_create_ensemble(len(meshes), arr, ctypes.byref(params), ctypes.byref(h))
         _check(rc, "gks2l_create")
         self._h = h
+        self._gate_variant = 0
         nbytes = ctypes.c_size_t(0)
         _check(L.gks2l_workspace_bytes(h, ctypes.byref(nbytes)), "gks2l_workspace_bytes")
         self.device = torch.device(device)
@@ -239,15 +241,24 @@ class Solver:
         return {"recon": ms[0], "iface": ms[1], "edge": ms[2], "update": ms[3], "step_begin": ms[4], "gate": ms[5]}
 
     def set_launch_shapes(self, shapes):
-        """Launch shapes (0..4) of the interface, edge and update kernels."""
-        b = (ctypes.c_int32 * 3)(*[int(x) for x in shapes])
+        """Launch shapes (0..4) of the interface, edge and update kernels and,
+        as a fourth entry, the gate kernel (0: mma.sync, 1: tcgen05, 2:
+        tcgen05 with more blocks; kept at the current choice when only three
+        are given)."""
+        shapes = [int(x) for x in shapes]
+        if len(shapes) == 3:
+            shapes.append(self._gate_variant)
+        b = (ctypes.c_int32 * 4)(*shapes)
         _check(load().gks2l_set_launch_shapes(self._h, ctypes.byref(b)), "gks2l_set_launch_shapes")
+        self._gate_variant = shapes[3]
 
     def autotune(self, n_steps=2):
         """Time each launch shape for n_steps steps (they advance the state);
-        keep the fastest per kernel and return the choices."""
-        b = (ctypes.c_int32 * 3)()
+        keep the fastest per kernel (and, with the gate on, the faster gate
+        kernel by whole steps) and return the four choices."""
+        b = (ctypes.c_int32 * 4)()
         _check(load().gks2l_autotune(self._h, int(n_steps), ctypes.byref(b)), "gks2l_autotune")
+        self._gate_variant = b[3]
         return list(b)
 
     def alu_peaks(self):

@@ -50,7 +50,7 @@ def test_autotune_advances_like_advance():
     prob.avg[3] += 0.01 * np.sin(np.arange(prob.mesh.n_tri))
     s = g.problem_solver(prob, precision=g.GKS2L_FP32)
     shapes = s.autotune(1)
-    assert len(shapes) == 3 and all(0 <= b < 5 for b in shapes)
+    assert len(shapes) == 4 and all(0 <= b < 5 for b in shapes[:3]) and shapes[3] == 0
     s.advance(6)
     a, gr = s.get_state()
     ref = g.problem_solver(prob, precision=g.GKS2L_FP32)

@@ -144,13 +144,19 @@ def test_harvest_matches_oracle(precision):
     assert np.array_equal(a0, a1) and np.array_equal(g0, g1)
 
 
+GATE_KERNELS = [0, 1, 2]   # mma.sync warp tiles, tcgen05 CTA tiles, the same with more blocks
+
+
+@pytest.mark.parametrize("variant", GATE_KERNELS)
 @pytest.mark.parametrize("case", ["ensemble", "dambreak"])
-def test_fused_gate_logits_match_oracle(case):
-    """Logits of the gate inside the reconstruction vs the oracle network on
-    the oracle's features of the same seeded state."""
+def test_fused_gate_logits_match_oracle(case, variant):
+    """Logits of the gate kernel (either variant) vs the oracle network on
+    the oracle's features of the same seeded state (392 and 800 cells: the
+    tensor-memory variant's last 128-cell tile is ragged)."""
     prob = inputs.ensemble_member(14, seed=31) if case == "ensemble" else inputs.interface_dambreak(20)
     P = params(10)
     s = g.problem_solver(prob, precision=g.GKS2L_FP64, indicator=g.GKS2L_INDICATOR_MLP)
+    s.set_launch_shapes([1, 1, 1, variant])
     s.set_mlp(P)
     logits = torch.empty(prob.mesh.n_tri, dtype=torch.float32, device=DEV)
     s.harvest(1e-2, logits=logits)
@@ -161,12 +167,34 @@ def test_fused_gate_logits_match_oracle(case):
     assert np.quantile(err, 0.99) <= 1e-4 and err.max() <= 2e-2, (np.quantile(err, 0.99), err.max())
 
 
+def test_gate_kernels_agree():
+    """The two gate kernels on the same state and network: logits equal up to
+    the FP32 accumulation order inside the MMAs, and so the same decisions
+    away from the threshold (5,408 cells with features everywhere, ragged
+    last tile)."""
+    prob = inputs.ensemble_member(52, seed=33)
+    P = params(11)
+    out = []
+    for variant in GATE_KERNELS:
+        s = g.problem_solver(prob, precision=g.GKS2L_FP32, indicator=g.GKS2L_INDICATOR_MLP)
+        s.set_launch_shapes([1, 1, 1, variant])
+        s.set_mlp(P)
+        logits = torch.empty(prob.mesh.n_tri, dtype=torch.float32, device=DEV)
+        s.harvest(1e-2, logits=logits)
+        out.append(logits.cpu().numpy().astype(np.float64))
+    for k in range(1, len(out)):
+        err = np.abs(out[k] - out[0]) / (1 + np.abs(out[0]))
+        assert err.max() <= 1e-3 and np.quantile(err, 0.99) <= 1e-5, (k, err.max(), np.quantile(err, 0.99))
+
+
+@pytest.mark.parametrize("variant", GATE_KERNELS)
 @pytest.mark.parametrize("case", ["smooth", "dambreak"])
-def test_all_smooth_gate_matches_oracle_linear_mask(case):
+def test_all_smooth_gate_matches_oracle_linear_mask(case, variant):
     """A gate that calls every cell smooth: the first stage (no decisions yet)
     is the plain method, every later one the P3 polynomial."""
     prob, n = (inputs.smooth_periodic(16), 100) if case == "smooth" else (inputs.interface_dambreak(16), 40)
     s = g.problem_solver(prob, precision=g.GKS2L_FP64, indicator=g.GKS2L_INDICATOR_MLP)
+    s.set_launch_shapes([1, 1, 1, variant])
     s.set_mlp(constant_gate(-30.0))
     s.advance(n)
     a, gr = s.get_state()
@@ -181,9 +209,11 @@ def test_all_smooth_gate_matches_oracle_linear_mask(case):
     assert ra <= 1e-11 and rg <= 1e-11, (ra, rg)
 
 
-def test_no_smooth_gate_is_the_plain_method():
+@pytest.mark.parametrize("variant", GATE_KERNELS)
+def test_no_smooth_gate_is_the_plain_method(variant):
     prob = inputs.interface_dambreak(16)
     s = g.problem_solver(prob, precision=g.GKS2L_FP32, indicator=g.GKS2L_INDICATOR_MLP)
+    s.set_launch_shapes([1, 1, 1, variant])
     s.set_mlp(constant_gate(30.0))
     s.advance(20)
     a, gr = s.get_state()

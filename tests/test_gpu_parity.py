@@ -81,6 +81,24 @@ def test_fp64_matches_oracle_to_t_end():
     assert ra <= 1e-11 and rg <= 1e-11, (ra, rg)
 
 
+def test_advance_to_an_end_time_stops_when_every_instance_arrives():
+    """One call asking for a million stages with an end time runs only the
+    steps needed (checked every 32 steps): no more than 64 stages beyond
+    stepping one step at a time, and the same state bit for bit."""
+    prob = inputs.smooth_periodic(16)
+    s1 = g.problem_solver(prob)
+    t1 = s1.advance(10 ** 6, t_end=prob.t_end)
+    a1, g1 = s1.get_state()
+    s2 = g.problem_solver(prob)
+    t2 = 0.0
+    while t2 < prob.t_end * (1 - 1e-12):
+        t2 = s2.advance(2, t_end=prob.t_end)
+    a2, g2 = s2.get_state()
+    assert t1 == t2 and abs(t1 - prob.t_end) < 1e-12
+    assert s2.stats()["stages"] <= s1.stats()["stages"] <= s2.stats()["stages"] + 64
+    assert np.array_equal(a1, a2) and np.array_equal(g1, g2)
+
+
 @pytest.mark.parametrize("case", ["dambreak", "lake", "translation", "rect_walls", "tiny_periodic", "tiny_walls"])
 def test_fp64_matches_oracle_cases(case):
     if case == "dambreak":
