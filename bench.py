@@ -342,9 +342,10 @@ def main():
                     help="profiling mode: one step of the workload with this many squares across its short "
                          "side, kernels launched one by one (for ncu captures of a small case)")
     ap.add_argument("--form", default="fp32_learned", choices=["fp32", "fp32_learned", "fp64"])
-    ap.add_argument("--gate-variant", type=int, default=0, choices=[0, 1, 2],
-                    help="profiling mode: the gate kernel (0: mma.sync warp tiles, 1: tcgen05 CTA tiles, "
-                         "2: tcgen05 with twice the blocks per SM)")
+    ap.add_argument("--gate-variant", type=int, default=0, choices=list(range(6)),
+                    help="profiling mode: the gate kernel (variant %% 3; 0: mma.sync warp tiles, 1: tcgen05 "
+                         "CTA tiles, 2: tcgen05 with twice the blocks per SM) and its placement (variant / 3; "
+                         "beside the edge kernels or the reconstruction)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -595,12 +596,17 @@ def main():
     roof = dict(roof)
     tpu = TRAFFIC_PER_UNIT.get(top)
     roof["traffic"] = tpu * units if tpu else None
-    roof["algorithmic_per_unit"] = recon_flops(rh["smooth_fraction"]) if top == "recon" else WORK_PER_UNIT[top][0]
+    fl_unit = recon_flops(rh["smooth_fraction"]) if top == "recon" else WORK_PER_UNIT[top][0]
+    by_unit = WORK_PER_UNIT[top][1]
+    # the bound's own measure: bytes for an HBM-bound kernel, flops otherwise
+    roof["algorithmic_per_unit"] = by_unit if roof["bound"] == "hbm" else fl_unit
+    roof["algorithmic_flops_per_unit"] = fl_unit
+    roof["algorithmic_bytes_per_unit"] = by_unit
     roof["units_per_launch"] = units
     roof["launch_ms"] = top_ms
     ex = EXECUTED_FP32_PER_UNIT.get(top)
     roof["executed_fp32_per_unit"] = ex
-    roof["overhead_executed_over_algorithmic"] = (ex / roof["algorithmic_per_unit"]) if ex else None
+    roof["overhead_executed_over_algorithmic"] = (ex / fl_unit) if ex else None
     roof["per_kernel"] = hf["roofline_frac"]
     timed = [x for x in kern if x != "step_begin"]
     ksum = sum(kern[x] for x in timed)

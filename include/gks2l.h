@@ -253,22 +253,26 @@ int gks2l_mlp_forward(const float *d_X, int32_t n, const float *d_params, float 
  * shapes (with the gate on, the edge shape applies to the fused interface and
  * edge kernel): 0: 64 threads per block, 1: 128 (default), 2: 256, 3: 128 threads
  * held to 64 registers (eight blocks per SM), 4: 128 threads held to 128
- * registers (four blocks per SM). shapes[3] picks the learned gate's kernel:
- * 0 (default): each warp takes 32 cells through mma.sync BF16 tiles, the
- * network in registers; 1: each 128-thread block takes 128 cells through
- * tcgen05 MMAs (M = 128, N = 32) with the accumulators in tensor memory and
- * the network in shared memory; 2: the same kernel with twice as many blocks
- * per SM. The gate kernels may differ in the last bit of a logit. */
+ * registers (four blocks per SM). shapes[3] picks the learned gate's kernel
+ * (shapes[3] % 3) and where it runs (shapes[3] / 3). Kernel 0 (default): each
+ * warp takes 32 cells through mma.sync BF16 tiles, the network in registers;
+ * 1: each 128-thread block takes 128 cells through tcgen05 MMAs (M = 128,
+ * N = 32) with the accumulators in tensor memory and the network in shared
+ * memory; 2: the same kernel with twice as many blocks per SM. The gate reads
+ * the stage's state and runs on a second stream, beside the edge kernels
+ * (placement 0) or beside the reconstruction (placement 1), joining before
+ * the cell update. The gate kernels may differ in the last bit of a logit;
+ * the placement changes no result. */
 #define GKS2L_LAUNCH_SHAPES 5
-#define GKS2L_GATE_VARIANTS 3
+#define GKS2L_GATE_VARIANTS 6
 int gks2l_set_launch_shapes(gks2l_ctx *ctx, const int32_t shapes[4]);
 
 /* Autotuner: advances the state by GKS2L_LAUNCH_SHAPES * n_steps full steps,
  * exactly as gks2l_advance would, timing the interface, edge and update
  * kernels in each shape (CUDA events on the bound stream); keeps the fastest
  * for each. With the gate on it then times GKS2L_GATE_VARIANTS * (n_steps + 1)
- * more steps, whole steps per gate kernel (the gate overlaps the edge
- * kernels, so its own time does not decide), and keeps the faster. Writes the
+ * more steps, whole steps per gate variant (the gate overlaps other kernels,
+ * so its own time does not decide), and keeps the fastest. Writes the
  * choices to shapes[4]. Requires a state and phase at a step boundary;
  * returns the run's status like gks2l_advance with t_out. */
 int gks2l_autotune(gks2l_ctx *ctx, int32_t n_steps, int32_t shapes[4]);
@@ -279,7 +283,7 @@ int gks2l_autotune(gks2l_ctx *ctx, int32_t n_steps, int32_t shapes[4]);
  * the mean duration of one launch of kernel k, in the order: reconstruction,
  * interface levels, edge solution, cell update (each averaged over both
  * stages), step start, troubled-cell gate (0 when it is off; run here in
- * sequence, in gks2l_advance beside the edge kernels). With the gate on, the
+ * sequence, in gks2l_advance on a second stream). With the gate on, the
  * interface levels and the edge solution run as one fused kernel, reported
  * in the edge slot, followed by a pass over the edges whose solution needs
  * the plane gradients, reported in the interface slot.

@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(128) k_gate(Dev d, Par p) {
     const float logit = mlp_tile32(F, X, GATE_LD, lane);
     const bool smooth = active && logit < F.threshold;
     const unsigned mask = __ballot_sync(FULL, smooth || !active);
-    if (lane == 0) d.gate_mask[tile] = mask;
+    if (lane == 0) d.gate_next[tile] = mask;
     if (p.logit_out && j < d.nt) p.logit_out[j] = logit;
     __syncwarp();   // the tile is rewritten next
   }
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(GATE_TC_M) k_gate_tc(Dev d, Par p) {
     const bool smooth = active && logit < S.threshold;
     const unsigned mask = __ballot_sync(FULL, smooth || !active);
     const int word = tile * (GATE_TC_M / TW) + warp;
-    if (lane == 0 && word < nword) d.gate_mask[word] = mask;
+    if (lane == 0 && word < nword) d.gate_next[word] = mask;
     if (p.logit_out && j < d.nt) p.logit_out[j] = logit;
     tc::fence_before();
   }
@@ -588,6 +588,8 @@ __device__ __forceinline__ void update_body(const Dev &d, const Par &p, int stag
     if (r > 0) ratio = r;
   }
   if (fl) atomicOr(d.status, fl);
+  // the gate has joined: its mask becomes the next reconstruction's
+  if (p.use_gate && ok && (j & (TW - 1)) == 0) d.gate_mask[j / TW] = d.gate_next[j / TW];
   if (stage != 2) return;
   reduce_cfl(d, ok, inst, ratio);
   if (ok && j == d.inst_first[inst]) d.t[inst] += d.dt[inst];
@@ -876,6 +878,7 @@ size_t layout(gks2l_ctx *c, char *base) {
   d.omg = k.take<char>(rs * 2 * cs);
   d.mlp = k.take<MlpDev>(1);
   d.gate_mask = k.take<unsigned>(cs / TW);
+  d.gate_next = k.take<unsigned>(cs / TW);
   d.wdev = k.take<float>(6 * cs);
   d.eL = k.take<int>(ne);
   d.eR = k.take<int>(ne);
@@ -1025,9 +1028,10 @@ Par make_par(const gks2l_ctx *c) {
 // overlap with the edge kernels)
 template <typename R>
 void launch_gate(gks2l_ctx *c, const Par &p, cudaStream_t st) {
-  const unsigned per_sm = c->shape[3] == 2 ? 2 * GATE_BLOCKS_PER_SM : GATE_BLOCKS_PER_SM;
+  const int kernel = c->shape[3] % 3;
+  const unsigned per_sm = kernel == 2 ? 2 * GATE_BLOCKS_PER_SM : GATE_BLOCKS_PER_SM;
   const unsigned nb = std::min(blocks(c->d.nt, 4 * TW), (unsigned)(c->n_sm * per_sm));
-  if (c->shape[3] >= 1) k_gate_tc<R><<<nb, GATE_TC_M, 0, st>>>(c->d, p);
+  if (kernel >= 1) k_gate_tc<R><<<nb, GATE_TC_M, 0, st>>>(c->d, p);
   else k_gate<R><<<nb, 128, 0, st>>>(c->d, p);
 }
 
@@ -1041,7 +1045,8 @@ void launch_recon(gks2l_ctx *c, const Par &p) {
 // 2: 256 threads (registers as the compiler likes), 3: 128 threads held to
 // 64 registers (eight blocks per SM), 4: 128 threads held to 128 registers
 constexpr int kShapes = 5;
-constexpr int kGateVariants = 3;   // gate kernel: 0 mma.sync warp tiles, 1 and 2 tcgen05 CTA tiles
+constexpr int kGateVariants = 6;   // gate kernel (variant % 3): 0 mma.sync warp tiles, 1 and 2 tcgen05 CTA
+                                   // tiles; placement (variant / 3): beside the edge kernels or the reconstruction
 
 #define GKS2L_SHAPE_SWITCH(cfg, KERNEL, n, st, ...)                                          \
   switch (cfg) {                                                                           \
@@ -1082,18 +1087,26 @@ void launch_update(gks2l_ctx *c, const Par &p, int stage, cudaStream_t st) {
   GKS2L_SHAPE_SWITCH(c->shape[2], k_update, n, st, c->d, p, stage)
 }
 
+// the gate on the second stream, from this point of the main stream on
+template <typename R>
+void fork_gate(gks2l_ctx *c, const Par &p) {
+  cudaEventRecord(c->ev_fork, c->stream);
+  cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+  launch_gate<R>(c, p, c->side);
+  cudaEventRecord(c->ev_join, c->side);
+}
+
 template <typename R>
 void launch_stage(gks2l_ctx *c, int stage) {
   Par p = make_par(c);
+  // The gate for the next stage reads this stage's state, which only
+  // k_update replaces, and writes its mask to a second buffer: it runs beside
+  // the reconstruction (gate variants 3-5) or beside the edge kernels (0-2)
+  // and joins before k_update, which copies the mask over.
+  const bool gate_early = p.use_gate && c->shape[3] >= 3;
+  if (gate_early) fork_gate<R>(c, p);
   launch_recon<R>(c, p);
-  if (p.use_gate) {
-    // the gate for the next stage reads this stage's state, which k_update
-    // replaces: it runs beside the edge kernels and joins before k_update
-    cudaEventRecord(c->ev_fork, c->stream);
-    cudaStreamWaitEvent(c->side, c->ev_fork, 0);
-    launch_gate<R>(c, p, c->side);
-    cudaEventRecord(c->ev_join, c->side);
-  }
+  if (p.use_gate && !gate_early) fork_gate<R>(c, p);
   if (p.use_gate) {
     launch_edge_fused<R>(c, p, stage, c->stream);
     launch_edge_deferred<R>(c, p, stage, c->stream);
@@ -1577,8 +1590,8 @@ int gks2l_autotune(gks2l_ctx *c, int32_t n_steps, int32_t shapes[4]) {
   }
   for (int k = 0; k < 3; k++) c->shape[k] = shapes[k] = pick[k];
   drop_graph(c);
-  // the gate runs beside the edge kernels on a second stream, so its variant
-  // is chosen by whole steps (captured graphs, CUDA events), not by its own time
+  // the gate runs beside other kernels on a second stream, so its variant is
+  // chosen by whole steps (captured graphs, CUDA events), not by its own time
   shapes[3] = c->shape[3];
   if (c->par.indicator == GKS2L_INDICATOR_MLP && c->has_mlp) {
     double best_g = INFINITY;

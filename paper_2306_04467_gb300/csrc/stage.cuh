@@ -77,6 +77,7 @@ struct Dev {
   void *omg;                // omega_H / gamma_H of eta1 [0] and h2 [1], type R
   const void *mlp;          // gate network, packed image (MlpDev)
   unsigned *gate_mask;      // per tile of 32 cells: bit i = cell i takes the linear weights
+  unsigned *gate_next;      // the gate's mask for the next reconstruction (k_update copies it over)
                             // (written by one reconstruction for the next)
   float *wdev;              // [6][cell] max_k |omega_k / gamma_k - 1| (harvesting)
   // per edge
@@ -123,20 +124,28 @@ template <> __host__ __device__ __forceinline__ float pv<float>(double, float f)
 
 // erf(x) given ex = e^{-x^2}, which the caller has formed already: in FP64
 // the library erf; in FP32 the rational approximation 7.1.26 of Abramowitz
-// and Stegun (Handbook of Mathematical Functions, after Hastings), erf(|x|) =
-// 1 - (a1 t + ... + a5 t^5) e^{-x^2}, t = 1/(1 + p |x|), absolute error at most
-// 1.5e-7 (near FP32 rounding), one reciprocal and five multiply-adds
+// and Stegun (Handbook of Mathematical Functions, after Hastings),
+// erf(|x|) = 1 - P(t) e^{-x^2}, P(t) = a1 t + ... + a5 t^5, t = 1/(1 + p|x|),
+// absolute error at most 1.5e-7, with P re-expanded about t = 1 in
+// s = 1 - t = p|x| t: P = b0 + b1 s + ... + b5 s^5, b_m = (-1)^m sum_k
+// C(k, m) a_k, and b0 (= sum a_k = 1 - 1e-9) taken as 1, a change far inside
+// that bound. Then erf(|x|) = (1 - e^{-x^2}) - e^{-x^2} s (b1 + ... + b5 s^4)
+// has no cancellation at small |x|: it is exact at zero and proportional to x
+// for tiny x (relative error 6e-6, the approximation's own slope), so the tiny
+// velocities of a state near rest keep their size in the half-space moments'
+// erf terms, which enter the deviation h-bar - h_b directly.
 template <typename R> __host__ __device__ __forceinline__ R erf_ex(R x, R ex);
 template <> __host__ __device__ __forceinline__ double erf_ex<double>(double x, double) { return erf(x); }
 template <> __host__ __device__ __forceinline__ float erf_ex<float>(float x, float ex) {
   const float ax = x < 0.f ? -x : x;
   const float t = 1.f / (1.f + 0.3275911f * ax);
-  float q = 1.061405429f;
-  q = q * t - 1.453152027f;
-  q = q * t + 1.421413741f;
-  q = q * t - 0.284496736f;
-  q = q * t + 0.254829592f;
-  const float e = 1.f - q * t * ex;
+  const float s = 0.3275911f * ax * t;
+  float q = -1.061405429f;
+  q = q * s + 3.853875118f;
+  q = q * s - 6.222859923f;
+  q = q * s + 5.874886615f;
+  q = q * s - 3.44449638f;
+  const float e = (1.f - ex) - ex * s * q;
   return x < 0.f ? -e : e;
 }
 template <typename R> __host__ __device__ __forceinline__ R r_erfc(R x);

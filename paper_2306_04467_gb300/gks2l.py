@@ -36,7 +36,7 @@ GKS2L_ENOTIMPL = -8
 GKS2L_ETOOBIG = -9
 GKS2L_ETIMEOUT = -10
 GKS2L_LAUNCH_SHAPES = 5
-GKS2L_GATE_VARIANTS = 3
+GKS2L_GATE_VARIANTS = 6
 
 # every entry point the header declares, with (restype, argtypes)
 _P = ctypes.c_void_p

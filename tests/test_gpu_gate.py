@@ -145,6 +145,7 @@ def test_harvest_matches_oracle(precision):
 
 
 GATE_KERNELS = [0, 1, 2]   # mma.sync warp tiles, tcgen05 CTA tiles, the same with more blocks
+GATE_VARIANTS = list(range(g.GKS2L_GATE_VARIANTS))   # each kernel beside the edge kernels, then beside the reconstruction
 
 
 @pytest.mark.parametrize("variant", GATE_KERNELS)
@@ -187,7 +188,7 @@ def test_gate_kernels_agree():
         assert err.max() <= 1e-3 and np.quantile(err, 0.99) <= 1e-5, (k, err.max(), np.quantile(err, 0.99))
 
 
-@pytest.mark.parametrize("variant", GATE_KERNELS)
+@pytest.mark.parametrize("variant", GATE_VARIANTS)
 @pytest.mark.parametrize("case", ["smooth", "dambreak"])
 def test_all_smooth_gate_matches_oracle_linear_mask(case, variant):
     """A gate that calls every cell smooth: the first stage (no decisions yet)
@@ -209,7 +210,7 @@ def test_all_smooth_gate_matches_oracle_linear_mask(case, variant):
     assert ra <= 1e-11 and rg <= 1e-11, (ra, rg)
 
 
-@pytest.mark.parametrize("variant", GATE_KERNELS)
+@pytest.mark.parametrize("variant", GATE_VARIANTS)
 def test_no_smooth_gate_is_the_plain_method(variant):
     prob = inputs.interface_dambreak(16)
     s = g.problem_solver(prob, precision=g.GKS2L_FP32, indicator=g.GKS2L_INDICATOR_MLP)
@@ -222,6 +223,32 @@ def test_no_smooth_gate_is_the_plain_method(variant):
     s2.advance(20)
     b, h = s2.get_state()
     assert np.array_equal(a, b) and np.array_equal(gr, h)
+
+
+@pytest.mark.parametrize("kernel", GATE_KERNELS)
+def test_gate_placement_changes_no_result(kernel):
+    """A network that calls some cells smooth and some not (its output bias
+    puts the oracle's median logit of the initial state at the threshold 1/2),
+    run beside the edge kernels and beside the reconstruction: the same
+    decisions reach the same reconstructions, so 20 stages agree bit for bit."""
+    prob = inputs.ensemble_member(16, seed=33)
+    P = params(10)
+    ref = mlp.forward(P, Oracle.from_problem(prob).gate_features(), use_bf16=True)
+    P[mlp.B3] -= np.float32(np.median(ref))
+    out = []
+    for variant in (kernel, kernel + 3):
+        s = g.problem_solver(prob, precision=g.GKS2L_FP32, indicator=g.GKS2L_INDICATOR_MLP,
+                             indicator_threshold=0.5)
+        s.set_launch_shapes([1, 1, 1, variant])
+        s.set_mlp(P)
+        s.advance(20)
+        a, gr = s.get_state()
+        st = s.stats()
+        assert st["status"] == 0
+        out.append((a, gr, st["smooth_fraction"]))
+    assert 0.0 < out[0][2] < 1.0, out[0][2]
+    assert out[0][2] == out[1][2]
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
 def test_set_mlp_rejects_bad_input():
