@@ -58,10 +58,15 @@ template <typename R> struct TileLayout {
   static constexpr unsigned BQ = P1 + 30 * TW * sizeof(R);
   static constexpr unsigned END = BQ + kBeta * TW * sizeof(R);
   static constexpr unsigned TILE = (END + 127) / 128 * 128;   // tile stride in global memory
-  static constexpr unsigned BAR = (END + 127) / 128 * 128;    // buffer stride in shared memory
   static constexpr unsigned TX_LINEAR = P1;                    // bytes of the first copy
-  static constexpr unsigned TX = END;                          // bytes of both copies
-  static_assert(2 * TW * NREC * sizeof(R) <= MM - LSQ, "side-record staging fits in the LSQ rows");
+  static constexpr unsigned TX2 = END - P1;                    // bytes of the second copy
+  // Shared memory holds the first copy; a tile with a troubled cell fetches
+  // the second after the P3 fit, into the space of the LSQ rows, which the
+  // side-record staging then follows.
+  static constexpr unsigned LATE = LSQ;
+  static constexpr unsigned STG = LATE + (TX2 + 127) / 128 * 128;
+  static constexpr unsigned BAR = (P1 + 127) / 128 * 128;      // the mbarrier, after the first copy
+  static_assert(STG + 2 * TW * NREC * sizeof(R) <= MM, "late rows and side-record staging fit in the LSQ rows");
   static_assert(P1 % 16 == 0 && END % 16 == 0, "bulk copies move multiples of 16 bytes");
 };
 
@@ -107,11 +112,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(void *bar, unsigned parity, un
 
 // ------------------------------------------------------------------ kernels
 // resident reconstruction blocks per SM the register budget is held to (in
-// FP32 seven, as many as the shared memory holds: a block per tile keeps 42
+// FP32 eight, as many as the registers allow: a block per tile keeps 48
 // warps per SM on the neighbour gathers; persistent blocks with two operator
 // buffers, fetching the next tile during the current one, halve the warps
 // and run slower)
-template <typename R> struct ReconOcc { static constexpr int value = 7; };
+template <typename R> struct ReconOcc { static constexpr int value = 8; };
 template <> struct ReconOcc<double> { static constexpr int value = 4; };
 template <typename R> constexpr unsigned recon_smem() { return TileLayout<R>::BAR + 16; }
 
@@ -127,15 +132,14 @@ __global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p)
   const bool gate_on = p.use_gate && !p.harvest;
   const unsigned lin_mask = gate_on ? d.gate_mask[blockIdx.x] : 0u;
   const bool all_linear = lin_mask == 0xffffffffu;
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    const unsigned char *src = (const unsigned char *)d.ops + (size_t)blockIdx.x * T::TILE;
+  const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+  const unsigned char *src = (const unsigned char *)d.ops + (size_t)blockIdx.x * T::TILE;
+  if (lead) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(all_linear ? T::TX_LINEAR : T::TX)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(T::TX_LINEAR)
                  : "memory");
     bulk_load(sm, src, T::TX_LINEAR, bar);
-    if (!all_linear) bulk_load(sm + T::P1, src + T::P1, T::TX - T::TX_LINEAR, bar);
   }
   // the cell's activity (a chain of two loads) resolves during the copies
   const int j = j0 + threadIdx.x, v = threadIdx.y;
@@ -148,14 +152,14 @@ __global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p)
     // (bounded, a second) so no copy outlives the block, and leave (all
     // threads); if they still have not landed, the block's shared memory may
     // yet be written after it exits, which a second bit records
-    if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(d.status, ST_TIMEOUT);
+    if (lead) atomicOr(d.status, ST_TIMEOUT);
     if (!landed && !mbar_wait_bounded(bar, 0, 1000000000ull)) atomicOr(d.status, ST_COPY_LOST);
     return;
   }
   CellOps<R> o;
   o.lsq = (const R *)(sm + T::LSQ);
-  o.p1 = (const R *)(sm + T::P1);
-  o.bq = (const R *)(sm + T::BQ);
+  o.p1 = (const R *)(sm + T::LATE);
+  o.bq = (const R *)(sm + T::LATE + (T::BQ - T::P1));
   o.mm = (const R *)(sm + T::MM);
   o.st = (const int *)(sm + T::ST);
   o.sx = (const int8_t *)(sm + T::SX);
@@ -174,9 +178,24 @@ __global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p)
     recon_gather<R>(d, o, j, v, rhs);
     recon_p3<R>(o, rhs, a);
   }
-  // every warp is done with the LSQ rows: their space stages the side records
+  // every warp is done with the LSQ rows: their space takes the late rows
+  // (tiles with a troubled cell) and stages the side records
   __syncthreads();
-  R *stg = (R *)(sm + T::LSQ);
+  if (!all_linear) {
+    if (lead) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(T::TX2)
+                   : "memory");
+      bulk_load(sm + T::LATE, src + T::P1, T::TX2, bar);
+    }
+    const bool late = mbar_wait_bounded(bar, 1, 1000000000ull);
+    if (!__syncthreads_and(late)) {
+      if (lead) atomicOr(d.status, ST_TIMEOUT);
+      if (!late && !mbar_wait_bounded(bar, 1, 1000000000ull)) atomicOr(d.status, ST_COPY_LOST);
+      return;
+    }
+  }
+  R *stg = (R *)(sm + T::STG);
   if (active) recon_finish<R>(d, p, o, j, v, rhs, a, linear, stg);
   if (v == 5 && j < d.nt) {
     // the constant words: 1/h_s and the bottom slope
