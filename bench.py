@@ -117,17 +117,22 @@ WORK_PER_UNIT = {
     "update": (400, 570),
 }
 # FP32 flops per unit that the hardware executes (ncu sm__sass_thread_inst_
-# executed_op_f{add,mul,fma} with FMA = 2, one step of the lake at 512 x 512
-# squares): reported beside the algorithmic counts as the overhead ratio.
-EXECUTED_FP32_PER_UNIT = {"recon": 2196, "gate": 257, "iface": 836, "edge": 5405, "edge_fused": 5719,
-                          "update": 317}
+# executed_op_f{add,mul,fma} with FMA = 2): reported beside the algorithmic
+# counts as the overhead ratio. recon, gate, edge_fused, update: one step of
+# the large configuration at 1416 x 177 squares (501,264 triangles), the
+# current kernels; iface and edge (the plain form's): the lake at 512 x 512
+# squares, captured before the edge kernels' last instruction cuts.
+EXECUTED_FP32_PER_UNIT = {"recon": 2214, "gate": 258, "iface": 836, "edge": 5405, "edge_fused": 5500,
+                          "update": 319}
 # Measured FMA-chain peaks of this GB300 pool (TFLOP/s, 2 flops per FMA); the
 # bench replaces them with the same run's own measurement.
 PEAK_TFLOPS = {"fp32": 76.5, "fp64": 1.254}
 # DRAM bytes per unit (dram__bytes_read.sum + dram__bytes_write.sum of the
-# same launches, per unit) from an ncu capture of the current kernels; none
-# is listed while the kernels have changed since the last capture.
-TRAFFIC_PER_UNIT = {}
+# same launches, per unit, mean of the two stages) from an ncu capture of the
+# current kernels on the large configuration at 1416 x 177 squares (inputs
+# larger than L2); the bench scales them to its launch by the units. A kernel
+# is listed only while it is unchanged since that capture.
+TRAFFIC_PER_UNIT = {"recon": 1040.0, "gate": 59.1, "edge_fused": 362.5, "update": 461.3}
 
 
 KERNEL_NAME = {"edge_fused": "k_edgef", "edge_deferred": "k_edge_deferred"}
@@ -139,6 +144,17 @@ def recon_flops(smooth_fraction):
     return RECON_P3 + (1.0 - smooth_fraction) * RECON_REST
 
 
+# the P1 candidate rows (30) and smoothness forms (45) of a cell, which only
+# a cell with the nonlinear weights reads
+RECON_LATE_BYTES = 4 * (30 + 45)
+
+
+def recon_bytes(smooth_fraction):
+    """Reconstruction bytes per cell when a fraction of the cells take the
+    linear weights and so need neither their P1 rows nor smoothness forms."""
+    return WORK_PER_UNIT["recon"][1] + (1.0 - smooth_fraction) * RECON_LATE_BYTES
+
+
 def roofline(form, kernel, units, ms, hbm_gbs, smooth_fraction=0.0):
     """Binding limit of one kernel launch: the slower of its algorithmic
     flops at the form's pipe peak (FP32 or FP64 FMA chains) and its
@@ -146,7 +162,7 @@ def roofline(form, kernel, units, ms, hbm_gbs, smooth_fraction=0.0):
     resource's rate in this launch."""
     fl, by = WORK_PER_UNIT[kernel]
     if kernel == "recon":
-        fl = recon_flops(smooth_fraction)
+        fl, by = recon_flops(smooth_fraction), recon_bytes(smooth_fraction)
     pipe = "fp64" if form == "fp64" else "fp32"
     if form == "fp64":
         by = 2 * by   # every R-typed record is a double
@@ -597,7 +613,7 @@ def main():
     tpu = TRAFFIC_PER_UNIT.get(top)
     roof["traffic"] = tpu * units if tpu else None
     fl_unit = recon_flops(rh["smooth_fraction"]) if top == "recon" else WORK_PER_UNIT[top][0]
-    by_unit = WORK_PER_UNIT[top][1]
+    by_unit = recon_bytes(rh["smooth_fraction"]) if top == "recon" else WORK_PER_UNIT[top][1]
     # the bound's own measure: bytes for an HBM-bound kernel, flops otherwise
     roof["algorithmic_per_unit"] = by_unit if roof["bound"] == "hbm" else fl_unit
     roof["algorithmic_flops_per_unit"] = fl_unit

@@ -50,9 +50,14 @@ def test_fp64_form_is_bound_by_the_fp64_pipe():
 
 
 def test_reconstruction_is_bound_by_its_bytes():
-    fl, by = bench.WORK_PER_UNIT["recon"]
+    """A cell with the nonlinear weights also reads its P1 rows and
+    smoothness forms (75 words): 1069 bytes per smooth cell, 1369 per
+    troubled one."""
+    assert bench.recon_bytes(1.0) == bench.WORK_PER_UNIT["recon"][1] == 1069
+    assert bench.recon_bytes(0.0) == 1069 + 300
     units, ms, hbm = 2_000_000, 0.55, 6800.0
     r = bench.roofline("fp32", "recon", units, ms, hbm, smooth_fraction=0.9)
+    by = 1069 + 0.1 * 300
     assert r["bound"] == "hbm" and r["kernel"] == "k_recon" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(by * units / (ms * 1e-3) / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / hbm)
