@@ -358,10 +358,11 @@ def main():
                     help="profiling mode: one step of the workload with this many squares across its short "
                          "side, kernels launched one by one (for ncu captures of a small case)")
     ap.add_argument("--form", default="fp32_learned", choices=["fp32", "fp32_learned", "fp64"])
-    ap.add_argument("--gate-variant", type=int, default=0, choices=list(range(6)),
+    ap.add_argument("--gate-variant", type=int, default=0, choices=list(range(12)),
                     help="profiling mode: the gate kernel (variant %% 3; 0: mma.sync warp tiles, 1: tcgen05 "
-                         "CTA tiles, 2: tcgen05 with twice the blocks per SM) and its placement (variant / 3; "
-                         "beside the edge kernels or the reconstruction)")
+                         "CTA tiles, 2: tcgen05 with twice the blocks per SM), its placement (variant / 3 %% 2; "
+                         "beside the edge kernels or the reconstruction) and the gated run's edge path "
+                         "(variant / 6; the fused pass or the plain interface and edge kernels)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -489,17 +490,33 @@ def main():
                     hg = torch.empty(12 * nt, dtype=torch.float64).pin_memory()
                     ha.copy_(torch.from_numpy(np.ascontiguousarray(prob.avg).ravel()))
                     hg.copy_(torch.from_numpy(np.ascontiguousarray(prob.grad).ravel()))
+                    oa = torch.empty(6 * nt, dtype=torch.float64).pin_memory()
+                    og = torch.empty(12 * nt, dtype=torch.float64).pin_memory()
                     n_e2e = max(2, K // 2)
+                    io_bytes = {"h2d_bytes_per_step": 18 * 8 * nt, "d2h_bytes_per_step": 18 * 8 * nt}
+                    # each step: the state in from pinned host memory, two
+                    # stages, the state out, as one pipelined call over the
+                    # steps (a step's copies overlap its neighbours' stages;
+                    # the first call makes the staging buffers, untimed)
+                    s.run_items([(ha, hg)], [(oa, og)], 2)
                     torch.cuda.synchronize(dev)
+                    t0 = time.perf_counter()
+                    s.run_items([(ha, hg)] * n_e2e, [(oa, og)] * n_e2e, 2)
+                    torch.cuda.synchronize(dev)
+                    el = max_over_ranks(time.perf_counter() - t0)
+                    res[form]["e2e"] = dict({"value": ws * nt * 2 * n_e2e / el, "unit": UNIT,
+                                             "api": "gks2l_run_items (pipelined host I/O)"}, **io_bytes)
+                    # the same steps one call at a time: set_state, advance, get_state
                     t0 = time.perf_counter()
                     for _ in range(n_e2e):
                         s.set_state_host_ptr(ha.data_ptr(), hg.data_ptr())
                         s.advance(2, sync=False)
-                        s.get_state_host_ptr(ha.data_ptr(), hg.data_ptr())
+                        s.get_state_host_ptr(oa.data_ptr(), og.data_ptr())
                     torch.cuda.synchronize(dev)
                     el = max_over_ranks(time.perf_counter() - t0)
-                    res[form]["e2e"] = {"value": ws * nt * 2 * n_e2e / el, "unit": UNIT,
-                                        "h2d_bytes_per_step": 18 * 8 * nt, "d2h_bytes_per_step": 18 * 8 * nt}
+                    res[form]["e2e_sequential"] = dict({"value": ws * nt * 2 * n_e2e / el, "unit": UNIT,
+                                                        "api": "gks2l_set_state, gks2l_advance, gks2l_get_state"},
+                                                       **io_bytes)
                 del s
                 torch.cuda.empty_cache()
         out = {"workload": describe(name, prob), "n_tri": nt, "n_edges": ne, "forms": {}}
@@ -507,13 +524,16 @@ def main():
             r = res[form]
             k = r["kernels"]
             sf = r["smooth_fraction"] if form == "fp32_learned" else 0.0
-            if form == "fp32_learned":
+            if form == "fp32_learned" and r["shapes"][3] < 6:
                 kern = {"recon": k["recon"], "edge_fused": k["edge"], "edge_deferred": k["iface"],
                         "update": k["update"], "gate": k["gate"], "step_begin": k["step_begin"]}
                 names = ("recon", "edge_fused", "update")
             else:
+                # the plain forms, and a gated run on the plain edge path
                 kern = {"recon": k["recon"], "iface": k["iface"], "edge": k["edge"], "update": k["update"],
                         "step_begin": k["step_begin"]}
+                if form == "fp32_learned":
+                    kern["gate"] = k["gate"]
                 names = ("recon", "iface", "edge", "update")
             units = {x: (nt if x in ("recon", "update", "gate") else ne) for x in kern}
             per = {x: roofline(form, x, units[x], kern[x], hbm, sf) for x in names}
@@ -659,6 +679,7 @@ def main():
         "alu_peaks_tflops": live_peaks,
         "clocks": rh["clocks"],
         "e2e": rh["e2e"],
+        "e2e_sequential": rh.get("e2e_sequential"),
         "gpu_launches": launches_per_step * args.steps,
         "cpu_baseline": cpu,
     }

@@ -187,6 +187,29 @@ int gks2l_get_state(gks2l_ctx *ctx, double *avg, double *grad);
 /* Copy the state to device arrays (caller order) on the bound stream. */
 int gks2l_get_state_device(gks2l_ctx *ctx, double *d_avg, double *d_grad);
 
+/* Pipelined host I/O (not part of the paper): n_items independent states,
+ * each set from host arrays as gks2l_set_state does, advanced n_stages
+ * stages (no end time) and read back to host arrays as gks2l_get_state does,
+ * in one call. Item i's host->device copy runs on an input copy stream and
+ * its device->host copy on an output copy stream, so with pinned host memory
+ * they overlap the computation of items i - 1 and i + 1 (pageable memory is
+ * accepted; its copies then serialise with the computation).
+ * in_avg[i], in_grad[i]: item i's state in the gks2l_set_state layout
+ * (in_grad itself or in_grad[i] may be NULL: zero gradients); out_avg[i],
+ * out_grad[i]: where its result goes, in the gks2l_get_state layout
+ * (out_grad or out_grad[i] may be NULL). Host arrays must stay valid until
+ * the call returns; an input and an output array must not overlap; one
+ * output array may serve several items (the copies run in item order, the
+ * last item's result remains). On return every copy has completed and the
+ * context holds the last item's state, as after gks2l_set_state and
+ * gks2l_advance. Returns GKS2L_EINVAL for n_items < 0, n_stages < 0 or a NULL
+ * in_avg[i] / out_avg[i]; otherwise the combined status of all items
+ * (GKS2L_ETIMEOUT, GKS2L_ENONFINITE, GKS2L_ENEGDEPTH as gks2l_advance).
+ * The first call allocates four staging buffers of 18 doubles per cell and
+ * two copy streams, kept until gks2l_destroy. */
+int gks2l_run_items(gks2l_ctx *ctx, int32_t n_items, int32_t n_stages, const double *const *in_avg,
+                    const double *const *in_grad, double *const *out_avg, double *const *out_grad);
+
 /* Statistics: each layer's mass sum_j |Omega_j| h_j (the quantity the
  * finite-volume form Eq. SWE-semi-discrete conserves), the time and last
  * step (Sec. 4's CFL step), the stages done and the device status;
@@ -260,11 +283,15 @@ int gks2l_mlp_forward(const float *d_X, int32_t n, const float *d_params, float 
  * N = 32) with the accumulators in tensor memory and the network in shared
  * memory; 2: the same kernel with twice as many blocks per SM. The gate reads
  * the stage's state and runs on a second stream, beside the edge kernels
- * (placement 0) or beside the reconstruction (placement 1), joining before
- * the cell update. The gate kernels may differ in the last bit of a logit;
- * the placement changes no result. */
+ * (placement 0, shapes[3] / 3 % 2) or beside the reconstruction (placement
+ * 1), joining before the cell update. shapes[3] / 6 picks the edge path of a
+ * gated run: 0, one fused interface-and-edge pass plus a deferred pass for
+ * the edges whose plane gradients carry weight; 1, the plain interface and
+ * edge kernels (faster when the gate calls few cells smooth). The gate
+ * kernels may differ in the last bit of a logit; placement and edge path
+ * change no result. */
 #define GKS2L_LAUNCH_SHAPES 5
-#define GKS2L_GATE_VARIANTS 6
+#define GKS2L_GATE_VARIANTS 12
 int gks2l_set_launch_shapes(gks2l_ctx *ctx, const int32_t shapes[4]);
 
 /* Autotuner: advances the state by GKS2L_LAUNCH_SHAPES * n_steps full steps,
@@ -283,7 +310,8 @@ int gks2l_autotune(gks2l_ctx *ctx, int32_t n_steps, int32_t shapes[4]);
  * the mean duration of one launch of kernel k, in the order: reconstruction,
  * interface levels, edge solution, cell update (each averaged over both
  * stages), step start, troubled-cell gate (0 when it is off; run here in
- * sequence, in gks2l_advance on a second stream). With the gate on, the
+ * sequence, in gks2l_advance on a second stream). With the gate on and the
+ * fused edge path (gate variants 0-5), the
  * interface levels and the edge solution run as one fused kernel, reported
  * in the edge slot, followed by a pass over the edges whose solution needs
  * the plane gradients, reported in the interface slot.

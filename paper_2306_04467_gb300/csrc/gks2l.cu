@@ -795,6 +795,8 @@ __global__ void k_scatter(int nt, int cs, int nvar, const int *perm, const doubl
   int c = perm[j];
   for (int v = 0; v < nvar; v++) dst[(size_t)v * nt + c] = src[(size_t)v * cs + j];
 }
+// the status word of one pipelined item, kept before the next item resets it
+__global__ void k_status_or(const int *st, int *acc) { *acc |= *st; }
 
 // FMA-chain throughput probe for the roofline denominators (measurement only)
 template <typename T>
@@ -853,6 +855,13 @@ struct gks2l_ctx {
   int64_t stages = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  // pipelined host I/O (gks2l_run_items, allocated on first use): two input
+  // and two output staging buffers of 18 * nt doubles, a copy stream for each
+  // direction and the events that hand the buffers between the streams
+  double *io_in[2] = {nullptr, nullptr}, *io_out[2] = {nullptr, nullptr};
+  int *d_status_any = nullptr;
+  cudaStream_t io_h2d = nullptr, io_d2h = nullptr;
+  cudaEvent_t ev_in_ready[2] = {}, ev_in_free[2] = {}, ev_out_ready[2] = {}, ev_out_free[2] = {};
   std::string err;
 };
 
@@ -1064,8 +1073,9 @@ void launch_recon(gks2l_ctx *c, const Par &p) {
 // 2: 256 threads (registers as the compiler likes), 3: 128 threads held to
 // 64 registers (eight blocks per SM), 4: 128 threads held to 128 registers
 constexpr int kShapes = 5;
-constexpr int kGateVariants = 6;   // gate kernel (variant % 3): 0 mma.sync warp tiles, 1 and 2 tcgen05 CTA
-                                   // tiles; placement (variant / 3): beside the edge kernels or the reconstruction
+constexpr int kGateVariants = 12;  // gate kernel (variant % 3): 0 mma.sync warp tiles, 1 and 2 tcgen05 CTA
+                                   // tiles; placement (variant / 3 % 2): beside the edge kernels or the
+                                   // reconstruction; edge path (variant / 6): fused, or the plain kernels
 
 #define GKS2L_SHAPE_SWITCH(cfg, KERNEL, n, st, ...)                                          \
   switch (cfg) {                                                                           \
@@ -1106,6 +1116,12 @@ void launch_update(gks2l_ctx *c, const Par &p, int stage, cudaStream_t st) {
   GKS2L_SHAPE_SWITCH(c->shape[2], k_update, n, st, c->d, p, stage)
 }
 
+// With the gate on, the interface levels and the edge solution run as one
+// fused pass plus the deferred edges (gate variants 0-5), or as the plain
+// interface and edge kernels (6-11), which a gate that calls few cells
+// smooth leaves faster.
+inline bool fused_edges(const gks2l_ctx *c, const Par &p) { return p.use_gate && c->shape[3] < 6; }
+
 // the gate on the second stream, from this point of the main stream on
 template <typename R>
 void fork_gate(gks2l_ctx *c, const Par &p) {
@@ -1120,13 +1136,13 @@ void launch_stage(gks2l_ctx *c, int stage) {
   Par p = make_par(c);
   // The gate for the next stage reads this stage's state, which only
   // k_update replaces, and writes its mask to a second buffer: it runs beside
-  // the reconstruction (gate variants 3-5) or beside the edge kernels (0-2)
-  // and joins before k_update, which copies the mask over.
-  const bool gate_early = p.use_gate && c->shape[3] >= 3;
+  // the reconstruction (gate variants 3-5, 9-11) or beside the edge kernels
+  // (0-2, 6-8) and joins before k_update, which copies the mask over.
+  const bool gate_early = p.use_gate && (c->shape[3] / 3) % 2 == 1;
   if (gate_early) fork_gate<R>(c, p);
   launch_recon<R>(c, p);
   if (p.use_gate && !gate_early) fork_gate<R>(c, p);
-  if (p.use_gate) {
+  if (fused_edges(c, p)) {
     launch_edge_fused<R>(c, p, stage, c->stream);
     launch_edge_deferred<R>(c, p, stage, c->stream);
   } else {
@@ -1478,6 +1494,96 @@ int gks2l_get_state_device(gks2l_ctx *c, double *d_avg, double *d_grad) {
   return GKS2L_OK;
 }
 
+// buffers, streams and events of gks2l_run_items, made on first use (each
+// piece once, so a call that failed part way completes them on the next)
+static int ensure_io(gks2l_ctx *c) {
+  if (c->io_h2d) return 0;
+  const size_t bytes = 18 * (size_t)c->prep.nt * sizeof(double);
+  for (int b = 0; b < 2; b++) {
+    if (!c->io_in[b]) CK(cudaMalloc((void **)&c->io_in[b], bytes));
+    if (!c->io_out[b]) CK(cudaMalloc((void **)&c->io_out[b], bytes));
+    for (cudaEvent_t *e : {&c->ev_in_ready[b], &c->ev_in_free[b], &c->ev_out_ready[b], &c->ev_out_free[b]})
+      if (!*e) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
+  if (!c->d_status_any) CK(cudaMalloc((void **)&c->d_status_any, sizeof(int)));
+  if (!c->io_d2h) CK(cudaStreamCreateWithFlags(&c->io_d2h, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&c->io_h2d, cudaStreamNonBlocking));
+  return 0;
+}
+
+// n stages from a state just set (phase 0), enqueued without any host wait
+static int enqueue_stages(gks2l_ctx *c, int n) {
+  if (n / 2 > 0) {
+    int rc = ensure_graph(c);
+    if (rc) return rc;
+  }
+  for (int s = 0; s < n / 2; s++) {
+    if (c->gexec) {
+      CK(cudaGraphLaunch(c->gexec, c->stream));
+    } else {
+      launch_step_begin(c);
+      launch_stage_any(c, 1);
+      launch_stage_any(c, 2);
+    }
+    c->stages += 2;
+  }
+  if (n % 2) {
+    launch_step_begin(c);
+    launch_stage_any(c, 1);
+    c->phase = 1;
+    c->stages++;
+  }
+  CK(cudaGetLastError());
+  return 0;
+}
+
+int gks2l_run_items(gks2l_ctx *c, int32_t n_items, int32_t n_stages, const double *const *in_avg,
+                    const double *const *in_grad, double *const *out_avg, double *const *out_grad) {
+  if (!c || n_items < 0 || n_stages < 0) return GKS2L_EINVAL;
+  if (n_items > 0 && (!in_avg || !out_avg)) return GKS2L_EINVAL;
+  for (int i = 0; i < n_items; i++)
+    if (!in_avg[i] || !out_avg[i]) return GKS2L_EINVAL;
+  if (!c->bound) return GKS2L_ESTATE;
+  if (n_items == 0) return GKS2L_OK;
+  int rc = ensure_io(c);
+  if (rc) return rc;
+  const size_t nt = c->prep.nt, na = 6 * nt * sizeof(double), ng = 12 * nt * sizeof(double);
+  // no end time: the steps' dt follow the CFL condition only
+  CK(cudaMemsetAsync(c->d_tend, 0, sizeof(double), c->stream));
+  CK(cudaMemsetAsync(c->d_status_any, 0, sizeof(int), c->stream));
+  if (n_stages / 2 > 0 && (rc = ensure_graph(c))) return rc;
+  for (int i = 0; i < n_items; i++) {
+    const int b = i & 1;
+    double *in = c->io_in[b], *out = c->io_out[b];
+    const bool gi = in_grad && in_grad[i], go = out_grad && out_grad[i];
+    // host -> device on the input stream, once item i - 2 has left the buffer
+    if (i >= 2) CK(cudaStreamWaitEvent(c->io_h2d, c->ev_in_free[b], 0));
+    CK(cudaMemcpyAsync(in, in_avg[i], na, cudaMemcpyHostToDevice, c->io_h2d));
+    if (gi) CK(cudaMemcpyAsync(in + 6 * nt, in_grad[i], ng, cudaMemcpyHostToDevice, c->io_h2d));
+    CK(cudaEventRecord(c->ev_in_ready[b], c->io_h2d));
+    // the item on the compute stream: set, advance, keep its status
+    CK(cudaStreamWaitEvent(c->stream, c->ev_in_ready[b], 0));
+    if ((rc = gks2l_set_state_device(c, in, gi ? in + 6 * nt : nullptr))) return rc;
+    CK(cudaEventRecord(c->ev_in_free[b], c->stream));
+    if ((rc = enqueue_stages(c, n_stages))) return rc;
+    k_status_or<<<1, 1, 0, c->stream>>>(c->d.status, c->d_status_any);
+    // into the output buffer once item i - 2's result has left it, then
+    // device -> host on the output stream
+    if (i >= 2) CK(cudaStreamWaitEvent(c->stream, c->ev_out_free[b], 0));
+    if ((rc = gks2l_get_state_device(c, out, go ? out + 6 * nt : nullptr))) return rc;
+    CK(cudaEventRecord(c->ev_out_ready[b], c->stream));
+    CK(cudaStreamWaitEvent(c->io_d2h, c->ev_out_ready[b], 0));
+    CK(cudaMemcpyAsync(out_avg[i], out, na, cudaMemcpyDeviceToHost, c->io_d2h));
+    if (go) CK(cudaMemcpyAsync(out_grad[i], out + 6 * nt, ng, cudaMemcpyDeviceToHost, c->io_d2h));
+    CK(cudaEventRecord(c->ev_out_free[b], c->io_d2h));
+  }
+  CK(cudaStreamSynchronize(c->io_d2h));
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, c->d_status_any, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return status_code(st);
+}
+
 int gks2l_stats(gks2l_ctx *c, gks2l_stats_t *out) {
   if (!c || !out) return GKS2L_EINVAL;
   if (!c->bound || !c->has_state) return GKS2L_ESTATE;
@@ -1517,7 +1623,7 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[6]) {
   for (int i = 0; i < 8; i++) CK(cudaEventCreate(&ev[i]));
   double acc[6] = {0, 0, 0, 0, 0, 0};
   Par p = make_par(c);
-  const bool f32 = c->par.precision == GKS2L_FP32;
+  const bool f32 = c->par.precision == GKS2L_FP32, fused = fused_edges(c, p);
   for (int s = 0; s < n_steps; s++) {
     CK(cudaEventRecord(ev[0], c->stream));
     launch_step_begin(c);
@@ -1531,11 +1637,11 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[6]) {
         if (f32) launch_gate<float>(c, p, c->stream);
         else launch_gate<double>(c, p, c->stream);
       }
-      // ungated: interface kernel between ev[7] and ev[4], edge kernel up to
-      // ev[5]; gated: fused kernel between ev[7] and ev[4] (reported as the
+      // plain edge path: interface kernel between ev[7] and ev[4], edge
+      // kernel up to ev[5]; fused path: fused kernel between ev[7] and ev[4] (reported as the
       // edge time), deferred pass up to ev[5] (reported in the interface slot)
       CK(cudaEventRecord(ev[7], c->stream));
-      if (p.use_gate) {
+      if (fused) {
         if (f32) launch_edge_fused<float>(c, p, stage, c->stream);
         else launch_edge_fused<double>(c, p, stage, c->stream);
       } else {
@@ -1543,7 +1649,7 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[6]) {
         else launch_iface<double>(c, c->stream);
       }
       CK(cudaEventRecord(ev[4], c->stream));
-      if (p.use_gate) {
+      if (fused) {
         if (f32) launch_edge_deferred<float>(c, p, stage, c->stream);
         else launch_edge_deferred<double>(c, p, stage, c->stream);
       } else {
@@ -1561,9 +1667,9 @@ int gks2l_profile_kernels(gks2l_ctx *c, int32_t n_steps, double ms[6]) {
       CK(cudaEventElapsedTime(&t, ev[3], ev[7]));
       acc[5] += t;
       CK(cudaEventElapsedTime(&t, ev[7], ev[4]));
-      acc[p.use_gate ? 2 : 1] += t;
+      acc[fused ? 2 : 1] += t;
       CK(cudaEventElapsedTime(&t, ev[4], ev[5]));
-      acc[p.use_gate ? 1 : 2] += t;
+      acc[fused ? 1 : 2] += t;
       CK(cudaEventElapsedTime(&t, ev[5], ev[6]));
       acc[3] += t;
     }
@@ -1762,6 +1868,15 @@ const char *gks2l_error_string(int code) {
 void gks2l_destroy(gks2l_ctx *c) {
   if (!c) return;
   drop_graph(c);
+  for (int b = 0; b < 2; b++) {
+    if (c->io_in[b]) cudaFree(c->io_in[b]);
+    if (c->io_out[b]) cudaFree(c->io_out[b]);
+    for (cudaEvent_t e : {c->ev_in_ready[b], c->ev_in_free[b], c->ev_out_ready[b], c->ev_out_free[b]})
+      if (e) cudaEventDestroy(e);
+  }
+  if (c->d_status_any) cudaFree(c->d_status_any);
+  if (c->io_h2d) cudaStreamDestroy(c->io_h2d);
+  if (c->io_d2h) cudaStreamDestroy(c->io_d2h);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);

@@ -36,7 +36,7 @@ GKS2L_ENOTIMPL = -8
 GKS2L_ETOOBIG = -9
 GKS2L_ETIMEOUT = -10
 GKS2L_LAUNCH_SHAPES = 5
-GKS2L_GATE_VARIANTS = 6
+GKS2L_GATE_VARIANTS = 12
 
 # every entry point the header declares, with (restype, argtypes)
 _P = ctypes.c_void_p
@@ -74,6 +74,7 @@ SIGNATURES = {
     "gks2l_advance": (_I, [_P, ctypes.c_int32, _D, ctypes.POINTER(_D)]),
     "gks2l_get_state": (_I, [_P, _P, _P]),
     "gks2l_get_state_device": (_I, [_P, _P, _P]),
+    "gks2l_run_items": (_I, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P]),
     "gks2l_stats": (_I, [_P, ctypes.POINTER(gks2l_stats_t)]),
     "gks2l_profile_kernels": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double * 6)]),
     "gks2l_set_launch_shapes": (_I, [_P, ctypes.POINTER(ctypes.c_int32 * 4)]),
@@ -228,6 +229,31 @@ class Solver:
                                              _P(grad.data_ptr()) if grad is not None else None),
                "gks2l_get_state_device")
 
+    def run_items(self, inputs, outputs, n_stages):
+        """Pipelined host I/O (gks2l_run_items): inputs[i] = (avg, grad) and
+        outputs[i] = (avg, grad) host arrays of item i, each a numpy float64
+        array (C-contiguous, the set_state / get_state layout), a CPU torch
+        tensor (pinned for overlap) or None for grad. Every item is set,
+        advanced n_stages stages and read back; the copies of neighbouring
+        items overlap the computation."""
+        n = len(inputs)
+        if len(outputs) != n:
+            raise ValueError("inputs and outputs differ in length")
+
+        def ptr(x, writable):
+            if x is None:
+                return None
+            if isinstance(x, np.ndarray):
+                if x.dtype != np.float64 or not x.flags.c_contiguous or (writable and not x.flags.writeable):
+                    raise ValueError("host arrays must be C-contiguous float64" + (" and writable" if writable else ""))
+                return x.ctypes.data
+            return x.data_ptr()
+
+        arr = ctypes.c_void_p * max(n, 1)
+        ia, ig = arr(*[ptr(a, False) for a, _ in inputs]), arr(*[ptr(g, False) for _, g in inputs])
+        oa, og = arr(*[ptr(a, True) for a, _ in outputs]), arr(*[ptr(g, True) for _, g in outputs])
+        _check(load().gks2l_run_items(self._h, n, int(n_stages), ia, ig, oa, og), "gks2l_run_items")
+
     def stats(self) -> dict:
         s = gks2l_stats_t()
         _check(load().gks2l_stats(self._h, ctypes.byref(s)), "gks2l_stats")
@@ -242,9 +268,9 @@ class Solver:
 
     def set_launch_shapes(self, shapes):
         """Launch shapes (0..4) of the interface, edge and update kernels and,
-        as a fourth entry, the gate kernel (0: mma.sync, 1: tcgen05, 2:
-        tcgen05 with more blocks; kept at the current choice when only three
-        are given)."""
+        as a fourth entry, the gate variant (0..11: kernel = v % 3, placement
+        = v // 3 % 2, edge path = v // 6; kept at the current choice when
+        only three are given)."""
         shapes = [int(x) for x in shapes]
         if len(shapes) == 3:
             shapes.append(self._gate_variant)

@@ -145,7 +145,9 @@ def test_harvest_matches_oracle(precision):
 
 
 GATE_KERNELS = [0, 1, 2]   # mma.sync warp tiles, tcgen05 CTA tiles, the same with more blocks
-GATE_VARIANTS = list(range(g.GKS2L_GATE_VARIANTS))   # each kernel beside the edge kernels, then beside the reconstruction
+# each kernel beside the edge kernels, then beside the reconstruction; both
+# with the fused edge pass, then with the plain edge kernels
+GATE_VARIANTS = list(range(g.GKS2L_GATE_VARIANTS))
 
 
 @pytest.mark.parametrize("variant", GATE_KERNELS)
@@ -229,14 +231,15 @@ def test_no_smooth_gate_is_the_plain_method(variant):
 def test_gate_placement_changes_no_result(kernel):
     """A network that calls some cells smooth and some not (its output bias
     puts the oracle's median logit of the initial state at the threshold 1/2),
-    run beside the edge kernels and beside the reconstruction: the same
-    decisions reach the same reconstructions, so 20 stages agree bit for bit."""
+    run beside the edge kernels and beside the reconstruction, each with the
+    fused edge pass and with the plain edge kernels: the same decisions reach
+    the same reconstructions and edges, so 20 stages agree bit for bit."""
     prob = inputs.ensemble_member(16, seed=33)
     P = params(10)
     ref = mlp.forward(P, Oracle.from_problem(prob).gate_features(), use_bf16=True)
     P[mlp.B3] -= np.float32(np.median(ref))
     out = []
-    for variant in (kernel, kernel + 3):
+    for variant in (kernel, kernel + 3, kernel + 6, kernel + 9):
         s = g.problem_solver(prob, precision=g.GKS2L_FP32, indicator=g.GKS2L_INDICATOR_MLP,
                              indicator_threshold=0.5)
         s.set_launch_shapes([1, 1, 1, variant])
@@ -247,8 +250,9 @@ def test_gate_placement_changes_no_result(kernel):
         assert st["status"] == 0
         out.append((a, gr, st["smooth_fraction"]))
     assert 0.0 < out[0][2] < 1.0, out[0][2]
-    assert out[0][2] == out[1][2]
-    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for o in out[1:]:
+        assert o[2] == out[0][2]
+        assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
 
 
 def test_set_mlp_rejects_bad_input():
