@@ -221,9 +221,10 @@ int gks2l_stats(gks2l_ctx *ctx, gks2l_stats_t *out);
  * cell whether the nonlinear WENO weights of the reconstruction would depart
  * from the linear ones; cells it calls smooth take the linear P3
  * reconstruction and a blending weight w = 1. The network runs on a second
- * stream beside each stage's interface and edge kernels, on the state that
- * stage reconstructed, and its decisions apply to the next reconstruction
- * (the first stage after gks2l_set_state or gks2l_set_mlp is the plain
+ * stream beside each stage's reconstruction or edge kernels, on the state
+ * that stage reconstructed, and its decisions apply to the next
+ * reconstruction; gks2l_set_state runs it once on the state it sets, for
+ * the first stage (the first stage after gks2l_set_mlp is the plain
  * method). gks2l_set_mlp creates that stream. Parameters are a float vector
  * of GKS2L_MLP_NPARAM entries:
  *   W1[32][24], b1[32], W2[32][32], b2[32], w3[32], b3, mean[24], inv_std[24]

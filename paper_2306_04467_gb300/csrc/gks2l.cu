@@ -1228,10 +1228,21 @@ int after_state(gks2l_ctx *c, const double *grad_caller) {
   CK(cudaMemsetAsync(c->d.dt, 0, sizeof(double) * c->d.ninst, c->stream));
   CK(cudaMemsetAsync(c->d.status, 0, sizeof(int), c->stream));
   CK(cudaMemsetAsync(c->d.gate_count, 0, 2 * sizeof(unsigned long long), c->stream));
-  // no gate decisions yet: the first reconstruction is the plain one
-  CK(cudaMemsetAsync(c->d.gate_mask, 0, (c->cs / TW) * sizeof(unsigned), c->stream));
   if (c->par.precision == GKS2L_FP32) k_cfl<float><<<blocks(c->d.nt, 128), 128, 0, c->stream>>>(c->d, p);
   else k_cfl<double><<<blocks(c->d.nt, 128), 128, 0, c->stream>>>(c->d, p);
+  if (p.use_gate) {
+    // the gate's decisions on the state just set serve the first
+    // reconstruction (every cell counts as active: no dt is known yet)
+    Par pg = p;
+    pg.all_active = 1;
+    if (c->par.precision == GKS2L_FP32) launch_gate<float>(c, pg, c->stream);
+    else launch_gate<double>(c, pg, c->stream);
+    CK(cudaMemcpyAsync(c->d.gate_mask, c->d.gate_next, (c->cs / TW) * sizeof(unsigned), cudaMemcpyDeviceToDevice,
+                       c->stream));
+  } else {
+    // no gate decisions: the first reconstruction is the plain one
+    CK(cudaMemsetAsync(c->d.gate_mask, 0, (c->cs / TW) * sizeof(unsigned), c->stream));
+  }
   CK(cudaGetLastError());
   c->phase = 0;
   c->stages = 0;

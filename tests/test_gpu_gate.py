@@ -212,6 +212,26 @@ def test_all_smooth_gate_matches_oracle_linear_mask(case, variant):
     assert ra <= 1e-11 and rg <= 1e-11, (ra, rg)
 
 
+def test_set_state_runs_the_gate_for_the_first_stage():
+    """A state set while the gate is on gets the gate's decisions on that
+    state for its first stage: with a gate that calls every cell smooth,
+    every stage (the first included) is the P3 polynomial."""
+    prob, n = inputs.smooth_periodic(16), 10
+    s = g.problem_solver(prob, precision=g.GKS2L_FP64, indicator=g.GKS2L_INDICATOR_MLP)
+    s.set_mlp(constant_gate(-30.0))
+    s.set_state(prob.avg, prob.grad)
+    s.advance(n)
+    a, gr = s.get_state()
+    st = s.stats()
+    assert st["status"] == 0 and st["smooth_fraction"] == 1.0
+    o = Oracle.from_problem(prob)
+    o.set_linear_mask(np.ones(prob.mesh.n_tri, np.uint8))
+    o.advance(n)
+    ao, go = o.get_state()
+    ra, rg = max_rel(prob, a, gr, ao, go)
+    assert ra <= 1e-11 and rg <= 1e-11, (ra, rg)
+
+
 @pytest.mark.parametrize("variant", GATE_VARIANTS)
 def test_no_smooth_gate_is_the_plain_method(variant):
     prob = inputs.interface_dambreak(16)
