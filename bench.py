@@ -358,11 +358,11 @@ def main():
                     help="profiling mode: one step of the workload with this many squares across its short "
                          "side, kernels launched one by one (for ncu captures of a small case)")
     ap.add_argument("--form", default="fp32_learned", choices=["fp32", "fp32_learned", "fp64"])
-    ap.add_argument("--gate-variant", type=int, default=0, choices=list(range(12)),
-                    help="profiling mode: the gate kernel (variant %% 3; 0: mma.sync warp tiles, 1: tcgen05 "
-                         "CTA tiles, 2: tcgen05 with twice the blocks per SM), its placement (variant / 3 %% 2; "
-                         "beside the edge kernels or the reconstruction) and the gated run's edge path "
-                         "(variant / 6; the fused pass or the plain interface and edge kernels)")
+    ap.add_argument("--gate-variant", type=int, default=0, choices=list(range(16)),
+                    help="profiling mode: the gate kernel (variant %% 4; 0: mma.sync warp tiles, 1: tcgen05 "
+                         "CTA tiles, 2 and 3: tcgen05 with two and four times the blocks per SM), its placement "
+                         "(variant / 4 %% 2; beside the edge kernels or the reconstruction) and the gated run's "
+                         "edge path (variant / 8; the fused pass or the plain interface and edge kernels)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -524,7 +524,7 @@ def main():
             r = res[form]
             k = r["kernels"]
             sf = r["smooth_fraction"] if form == "fp32_learned" else 0.0
-            if form == "fp32_learned" and r["shapes"][3] < 6:
+            if form == "fp32_learned" and r["shapes"][3] < 8:
                 kern = {"recon": k["recon"], "edge_fused": k["edge"], "edge_deferred": k["iface"],
                         "update": k["update"], "gate": k["gate"], "step_begin": k["step_begin"]}
                 names = ("recon", "edge_fused", "update")

@@ -277,22 +277,23 @@ int gks2l_mlp_forward(const float *d_X, int32_t n, const float *d_params, float 
  * shapes (with the gate on, the edge shape applies to the fused interface and
  * edge kernel): 0: 64 threads per block, 1: 128 (default), 2: 256, 3: 128 threads
  * held to 64 registers (eight blocks per SM), 4: 128 threads held to 128
- * registers (four blocks per SM). shapes[3] picks the learned gate's kernel
- * (shapes[3] % 3) and where it runs (shapes[3] / 3). Kernel 0 (default): each
- * warp takes 32 cells through mma.sync BF16 tiles, the network in registers;
- * 1: each 128-thread block takes 128 cells through tcgen05 MMAs (M = 128,
- * N = 32) with the accumulators in tensor memory and the network in shared
- * memory; 2: the same kernel with twice as many blocks per SM. The gate reads
- * the stage's state and runs on a second stream, beside the edge kernels
- * (placement 0, shapes[3] / 3 % 2) or beside the reconstruction (placement
- * 1), joining before the cell update. shapes[3] / 6 picks the edge path of a
- * gated run: 0, one fused interface-and-edge pass plus a deferred pass for
- * the edges whose plane gradients carry weight; 1, the plain interface and
- * edge kernels (faster when the gate calls few cells smooth). The gate
+ * registers (four blocks per SM). shapes[3] picks the learned gate's variant:
+ * its kernel (shapes[3] % 4): 0 (default), each warp takes 32 cells through
+ * mma.sync BF16 tiles, the network in registers; 1, each 128-thread block
+ * takes 128 cells through tcgen05 MMAs (M = 128, N = 32) with the
+ * accumulators in tensor memory and the network in shared memory; 2 and 3,
+ * the same kernel with two and four times as many blocks per SM. Its
+ * placement (shapes[3] / 4 % 2): the gate reads the stage's state and runs on
+ * a second stream beside the edge kernels (0) or beside the reconstruction
+ * (1), joining before the cell update. The gated run's edge path
+ * (shapes[3] / 8): 0, one fused interface-and-edge pass plus a deferred pass
+ * for the edges whose plane gradients carry weight; 1, the plain interface
+ * and edge kernels (faster when the gate calls few cells smooth). The gate
  * kernels may differ in the last bit of a logit; placement and edge path
  * change no result. */
 #define GKS2L_LAUNCH_SHAPES 5
-#define GKS2L_GATE_VARIANTS 12
+#define GKS2L_GATE_KERNELS 4
+#define GKS2L_GATE_VARIANTS 16
 int gks2l_set_launch_shapes(gks2l_ctx *ctx, const int32_t shapes[4]);
 
 /* Autotuner: advances the state by GKS2L_LAUNCH_SHAPES * n_steps full steps,
@@ -312,7 +313,7 @@ int gks2l_autotune(gks2l_ctx *ctx, int32_t n_steps, int32_t shapes[4]);
  * interface levels, edge solution, cell update (each averaged over both
  * stages), step start, troubled-cell gate (0 when it is off; run here in
  * sequence, in gks2l_advance on a second stream). With the gate on and the
- * fused edge path (gate variants 0-5), the
+ * fused edge path (gate variants 0-7), the
  * interface levels and the edge solution run as one fused kernel, reported
  * in the edge slot, followed by a pass over the edges whose solution needs
  * the plane gradients, reported in the interface slot.

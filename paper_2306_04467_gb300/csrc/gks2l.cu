@@ -1050,14 +1050,24 @@ Par make_par(const gks2l_ctx *c) {
 }
 
 
-// the gate in its chosen variant: 0: warp tiles of 32 cells on mma.sync,
+// gate variants: kernel (variant % 4): 0 mma.sync warp tiles, 1-3 tcgen05 CTA
+// tiles at 1, 2 and 4 times the blocks per SM; placement (variant / 4 % 2):
+// beside the edge kernels or the reconstruction; edge path (variant / 8):
+// the fused pass or the plain kernels
+constexpr int kGateKernels = 4, kGateVariants = 4 * kGateKernels;
+inline int gate_kernel(int v) { return v % kGateKernels; }
+inline bool gate_beside_recon(int v) { return (v / kGateKernels) % 2 == 1; }
+inline bool gate_plain_edges(int v) { return v >= 2 * kGateKernels; }
+
+// the gate in its chosen kernel: 0: warp tiles of 32 cells on mma.sync,
 // 1: CTA tiles of 128 cells on tcgen05 with tensor-memory accumulators,
-// 2: the same with twice the CTAs per SM (more gathers in flight, more
-// overlap with the edge kernels)
+// 2 and 3: the same with two and four times the CTAs per SM (more gathers
+// in flight; at four, eight CTAs fill an SM's registers and hold 256 of its
+// 512 tensor-memory columns)
 template <typename R>
 void launch_gate(gks2l_ctx *c, const Par &p, cudaStream_t st) {
-  const int kernel = c->shape[3] % 3;
-  const unsigned per_sm = kernel == 2 ? 2 * GATE_BLOCKS_PER_SM : GATE_BLOCKS_PER_SM;
+  const int kernel = gate_kernel(c->shape[3]);
+  const unsigned per_sm = GATE_BLOCKS_PER_SM * (kernel == 3 ? 4 : kernel == 2 ? 2 : 1);
   const unsigned nb = std::min(blocks(c->d.nt, 4 * TW), (unsigned)(c->n_sm * per_sm));
   if (kernel >= 1) k_gate_tc<R><<<nb, GATE_TC_M, 0, st>>>(c->d, p);
   else k_gate<R><<<nb, 128, 0, st>>>(c->d, p);
@@ -1073,9 +1083,6 @@ void launch_recon(gks2l_ctx *c, const Par &p) {
 // 2: 256 threads (registers as the compiler likes), 3: 128 threads held to
 // 64 registers (eight blocks per SM), 4: 128 threads held to 128 registers
 constexpr int kShapes = 5;
-constexpr int kGateVariants = 12;  // gate kernel (variant % 3): 0 mma.sync warp tiles, 1 and 2 tcgen05 CTA
-                                   // tiles; placement (variant / 3 % 2): beside the edge kernels or the
-                                   // reconstruction; edge path (variant / 6): fused, or the plain kernels
 
 #define GKS2L_SHAPE_SWITCH(cfg, KERNEL, n, st, ...)                                          \
   switch (cfg) {                                                                           \
@@ -1117,10 +1124,10 @@ void launch_update(gks2l_ctx *c, const Par &p, int stage, cudaStream_t st) {
 }
 
 // With the gate on, the interface levels and the edge solution run as one
-// fused pass plus the deferred edges (gate variants 0-5), or as the plain
-// interface and edge kernels (6-11), which a gate that calls few cells
+// fused pass plus the deferred edges (gate variants 0-7), or as the plain
+// interface and edge kernels (8-15), which a gate that calls few cells
 // smooth leaves faster.
-inline bool fused_edges(const gks2l_ctx *c, const Par &p) { return p.use_gate && c->shape[3] < 6; }
+inline bool fused_edges(const gks2l_ctx *c, const Par &p) { return p.use_gate && !gate_plain_edges(c->shape[3]); }
 
 // the gate on the second stream, from this point of the main stream on
 template <typename R>
@@ -1136,9 +1143,9 @@ void launch_stage(gks2l_ctx *c, int stage) {
   Par p = make_par(c);
   // The gate for the next stage reads this stage's state, which only
   // k_update replaces, and writes its mask to a second buffer: it runs beside
-  // the reconstruction (gate variants 3-5, 9-11) or beside the edge kernels
-  // (0-2, 6-8) and joins before k_update, which copies the mask over.
-  const bool gate_early = p.use_gate && (c->shape[3] / 3) % 2 == 1;
+  // the reconstruction or beside the edge kernels (the variant's placement)
+  // and joins before k_update, which copies the mask over.
+  const bool gate_early = p.use_gate && gate_beside_recon(c->shape[3]);
   if (gate_early) fork_gate<R>(c, p);
   launch_recon<R>(c, p);
   if (p.use_gate && !gate_early) fork_gate<R>(c, p);

@@ -36,7 +36,8 @@ GKS2L_ENOTIMPL = -8
 GKS2L_ETOOBIG = -9
 GKS2L_ETIMEOUT = -10
 GKS2L_LAUNCH_SHAPES = 5
-GKS2L_GATE_VARIANTS = 12
+GKS2L_GATE_KERNELS = 4
+GKS2L_GATE_VARIANTS = 16
 
 # every entry point the header declares, with (restype, argtypes)
 _P = ctypes.c_void_p
@@ -268,8 +269,8 @@ class Solver:
 
     def set_launch_shapes(self, shapes):
         """Launch shapes (0..4) of the interface, edge and update kernels and,
-        as a fourth entry, the gate variant (0..11: kernel = v % 3, placement
-        = v // 3 % 2, edge path = v // 6; kept at the current choice when
+        as a fourth entry, the gate variant (0..15: kernel = v % 4, placement
+        = v // 4 % 2, edge path = v // 8; kept at the current choice when
         only three are given)."""
         shapes = [int(x) for x in shapes]
         if len(shapes) == 3:

@@ -144,7 +144,8 @@ def test_harvest_matches_oracle(precision):
     assert np.array_equal(a0, a1) and np.array_equal(g0, g1)
 
 
-GATE_KERNELS = [0, 1, 2]   # mma.sync warp tiles, tcgen05 CTA tiles, the same with more blocks
+# mma.sync warp tiles, tcgen05 CTA tiles, the same with two and four times the blocks
+GATE_KERNELS = list(range(g.GKS2L_GATE_KERNELS))
 # each kernel beside the edge kernels, then beside the reconstruction; both
 # with the fused edge pass, then with the plain edge kernels
 GATE_VARIANTS = list(range(g.GKS2L_GATE_VARIANTS))
@@ -259,7 +260,8 @@ def test_gate_placement_changes_no_result(kernel):
     ref = mlp.forward(P, Oracle.from_problem(prob).gate_features(), use_bf16=True)
     P[mlp.B3] -= np.float32(np.median(ref))
     out = []
-    for variant in (kernel, kernel + 3, kernel + 6, kernel + 9):
+    K = g.GKS2L_GATE_KERNELS
+    for variant in (kernel, kernel + K, kernel + 2 * K, kernel + 3 * K):
         s = g.problem_solver(prob, precision=g.GKS2L_FP32, indicator=g.GKS2L_INDICATOR_MLP,
                              indicator_threshold=0.5)
         s.set_launch_shapes([1, 1, 1, variant])
