@@ -492,7 +492,7 @@ def main():
                     hg.copy_(torch.from_numpy(np.ascontiguousarray(prob.grad).ravel()))
                     oa = torch.empty(6 * nt, dtype=torch.float64).pin_memory()
                     og = torch.empty(12 * nt, dtype=torch.float64).pin_memory()
-                    n_e2e = max(2, K // 2)
+                    n_e2e = K
                     io_bytes = {"h2d_bytes_per_step": 18 * 8 * nt, "d2h_bytes_per_step": 18 * 8 * nt}
                     # each step: the state in from pinned host memory, two
                     # stages, the state out, as one pipelined call over the

@@ -1555,16 +1555,10 @@ static int enqueue_stages(gks2l_ctx *c, int n) {
   return 0;
 }
 
-int gks2l_run_items(gks2l_ctx *c, int32_t n_items, int32_t n_stages, const double *const *in_avg,
-                    const double *const *in_grad, double *const *out_avg, double *const *out_grad) {
-  if (!c || n_items < 0 || n_stages < 0) return GKS2L_EINVAL;
-  if (n_items > 0 && (!in_avg || !out_avg)) return GKS2L_EINVAL;
-  for (int i = 0; i < n_items; i++)
-    if (!in_avg[i] || !out_avg[i]) return GKS2L_EINVAL;
-  if (!c->bound) return GKS2L_ESTATE;
-  if (n_items == 0) return GKS2L_OK;
-  int rc = ensure_io(c);
-  if (rc) return rc;
+// the items' copies and stages, enqueued on the three streams
+static int enqueue_items(gks2l_ctx *c, int32_t n_items, int32_t n_stages, const double *const *in_avg,
+                         const double *const *in_grad, double *const *out_avg, double *const *out_grad) {
+  int rc;
   const size_t nt = c->prep.nt, na = 6 * nt * sizeof(double), ng = 12 * nt * sizeof(double);
   // no end time: the steps' dt follow the CFL condition only
   CK(cudaMemsetAsync(c->d_tend, 0, sizeof(double), c->stream));
@@ -1595,7 +1589,26 @@ int gks2l_run_items(gks2l_ctx *c, int32_t n_items, int32_t n_stages, const doubl
     if (go) CK(cudaMemcpyAsync(out_grad[i], out + 6 * nt, ng, cudaMemcpyDeviceToHost, c->io_d2h));
     CK(cudaEventRecord(c->ev_out_free[b], c->io_d2h));
   }
-  CK(cudaStreamSynchronize(c->io_d2h));
+  return 0;
+}
+
+int gks2l_run_items(gks2l_ctx *c, int32_t n_items, int32_t n_stages, const double *const *in_avg,
+                    const double *const *in_grad, double *const *out_avg, double *const *out_grad) {
+  if (!c || n_items < 0 || n_stages < 0) return GKS2L_EINVAL;
+  if (n_items > 0 && (!in_avg || !out_avg)) return GKS2L_EINVAL;
+  for (int i = 0; i < n_items; i++)
+    if (!in_avg[i] || !out_avg[i]) return GKS2L_EINVAL;
+  if (!c->bound) return GKS2L_ESTATE;
+  if (n_items == 0) return GKS2L_OK;
+  int rc = ensure_io(c);
+  if (rc) return rc;
+  rc = enqueue_items(c, n_items, n_stages, in_avg, in_grad, out_avg, out_grad);
+  // whatever was enqueued finishes before the caller's host arrays are
+  // handed back, on the error path too
+  const cudaError_t e[3] = {cudaStreamSynchronize(c->io_h2d), cudaStreamSynchronize(c->io_d2h),
+                            cudaStreamSynchronize(c->stream)};
+  if (rc) return rc;
+  for (cudaError_t x : e) CK(x);
   int st = 0;
   CK(cudaMemcpyAsync(&st, c->d_status_any, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
