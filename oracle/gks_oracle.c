@@ -26,6 +26,12 @@
  * for them parity is unpinned against the paper (parity unpinned), fixed by
  * the readings and by the weights' pinned behaviour (exactly linear on
  * smooth data, collapsing at a jump).
+ *
+ * One addition is not in the paper: an off-by-default positivity option
+ * (orc_set_positivity; positivity_scale and the velocity bound in the edge
+ * loop) for the large-jump cases the method as read cannot carry. It is
+ * pinned by a smooth flow it leaves unchanged bit for bit and by Riemann
+ * problem II's conservation and bounds.
  */
 #include <math.h>
 #include <stdio.h>
@@ -149,6 +155,8 @@ typedef struct {
   double *xy; int *tri; signed char *tri_bc;
   double period[2];
   double g, chi, cfl, eps, eps_num, gam_hi, weno_eps;
+  double pos_floor;                      /* positivity option (not in the paper): 0 = off */
+  unsigned char *pos_scaled;             /* 2 per cell: layer (0 lower, 1 upper) scaled this stage */
   /* geometry per cell */
   double *area, *cx, *cy, *hs, *dX, *bmean;  /* bmean: cell average of the P1 bottom */
   double *bgrad;                         /* 2 per cell */
@@ -975,6 +983,52 @@ static void to_local_side(const double val[NVAR], const double grd[NVAR][2], int
   }
 }
 
+/* Positivity option (not in the paper, which states no limiter; off by      */
+/* default, pos_floor = 0). After the reconstruction, a layer whose depth at  */
+/* one of the cell's six edge Gauss points falls below pos_floor times the    */
+/* cell's average depth has its depth and both discharge polynomials pulled  */
+/* toward their cell averages by one factor theta, so that the least point    */
+/* depth meets the floor (averages unchanged, so conservation is untouched); */
+/* for the lower layer the depth is eta1 - B, so the bottom's linear part is  */
+/* kept out of the scaling.                                                   */
+static void positivity_scale(orc_t *o) {
+  if (!o->pos_scaled) o->pos_scaled = calloc(2 * (size_t)o->nt, 1);
+  for (int j = 0; j < o->nt; j++) {
+    o->pos_scaled[2 * j] = o->pos_scaled[2 * j + 1] = 0;
+    double hmin[2] = {INFINITY, INFINITY};   /* [0] lower layer h1, [1] upper layer h2 */
+    for (int f = 0; f < 3; f++) {
+      const edge_t *E = &o->edge[o->face_edge[IDX2(j, f)]];
+      for (int q = 0; q < 2; q++) {
+        double x[2], val[NVAR], grd[NVAR][2];
+        if (o->face_side[IDX2(j, f)] > 0) { x[0] = E->xq[q][0]; x[1] = E->xq[q][1]; }
+        else aff_apply_inv(&E->R.T, E->xq[q], x);
+        eval_cell(o, j, x, val, grd);
+        hmin[0] = fmin(hmin[0], val[3] - E->bq[q]);
+        hmin[1] = fmin(hmin[1], val[0]);
+      }
+    }
+    for (int l = 0; l < 2; l++) {
+      const int v = l == 0 ? 3 : 0;
+      const double hbar = o->coef[(j * NVAR + v) * NB] - (l == 0 ? o->bmean[j] : 0.0);
+      const double fl = o->pos_floor * hbar;
+      /* a layer whose point depths dip below half its average has its point */
+      /* velocities bounded at its edges (the discharge slope of a steep jump */
+      /* would otherwise meet a small depth)                                 */
+      if (hmin[l] < 0.5 * hbar) o->pos_scaled[2 * j + l] = 1;
+      if (hmin[l] >= fl) continue;
+      const double th = fmax(0.0, (hbar - fl) / (hbar - hmin[l]));
+      for (int m = 0; m < 3; m++) {
+        double *cf = &o->coef[(j * NVAR + v + m) * NB];
+        for (int k = 1; k < NB; k++) cf[k] *= th;
+      }
+      if (l == 0) {   /* eta1 = h1 + B: B's linear part stays */
+        o->coef[(j * NVAR + 3) * NB + 1] += (1 - th) * o->hs[j] * o->bgrad[2 * j];
+        o->coef[(j * NVAR + 3) * NB + 2] += (1 - th) * o->hs[j] * o->bgrad[2 * j + 1];
+      }
+    }
+  }
+}
+
 static void stage(orc_t *o, int st) {
   const double dt = o->dt;
   /* the fit interval (reading R20): both stages fit the value and time     */
@@ -984,6 +1038,7 @@ static void stage(orc_t *o, int st) {
   const double delta = dt;
   const double G = o->g;
   reconstruct(o);
+  if (o->pos_floor > 0) positivity_scale(o);
   /* interface values at each Gauss point, both sides (R3, R7) */
   int ne = o->ne;
   double (*vl)[2][NVAR] = malloc(sizeof(double) * ne * 2 * NVAR);
@@ -1065,6 +1120,24 @@ static void stage(orc_t *o, int st) {
         side_t s[2];
         for (int sd = 0; sd < 2; sd++) {
           to_local_side(V[sd], Gd[sd], base, n, &s[sd]);
+          const int own_cell = sd == 0 ? E->L : E->R.cell, lay = base == 3 ? 0 : 1;
+          if (o->pos_floor > 0 && o->pos_scaled[2 * own_cell + lay]) {
+            /* positivity option, on a side whose depth polynomial was        */
+            /* scaled: the point velocity kept within the two cells' average  */
+            /* velocities of the layer (R's seen through its image), so a    */
+            /* depth pulled up toward the floor cannot carry the discharge   */
+            /* slope of a jump into a spurious vacuum                         */
+            const double hL = o->avg[E->L * NVAR + base], hR = o->avg[E->R.cell * NVAR + base];
+            const double uL[2] = {o->avg[E->L * NVAR + base + 1] / hL, o->avg[E->L * NVAR + base + 2] / hL};
+            const double uR0[2] = {o->avg[E->R.cell * NVAR + base + 1] / hR,
+                                   o->avg[E->R.cell * NVAR + base + 2] / hR};
+            double uR[2];
+            rot_vec(&E->R.T, uR0, uR);
+            const double nl = uL[0] * n[0] + uL[1] * n[1], nr = uR[0] * n[0] + uR[1] * n[1];
+            const double tl = uL[0] * t[0] + uL[1] * t[1], tr = uR[0] * t[0] + uR[1] * t[1];
+            s[sd].U = fmin(fmax(s[sd].U, fmin(nl, nr)), fmax(nl, nr));
+            s[sd].V = fmin(fmax(s[sd].V, fmin(tl, tr)), fmax(tl, tr));
+          }
           /* acceleration (Eq. bgk-phi, Sec. 2.3) with the blended derivative of */
           /* the other layer's depth                                              */
           double ht[2], ph[2];
@@ -1239,6 +1312,7 @@ orc_t *orc_create(int nv, const double *xy, int nt, const int *tri, const signed
 }
 
 void orc_destroy(orc_t *o) {
+  if (o) free(o->pos_scaled);
   if (!o) return;
   void *ptrs[] = {o->xy, o->tri, o->tri_bc, o->bvert, o->area, o->cx, o->cy, o->hs, o->dX, o->bmean,
                   o->bgrad, o->mean_m, o->face, o->face_edge, o->face_side, o->navg, o->avg_img, o->M,
@@ -1316,6 +1390,9 @@ void orc_cell_geometry(const orc_t *o, double *area, double *cx, double *cy) {
 
 /* pins: reconstruct from the current state, then evaluate cell c's polynomials */
 void orc_reconstruct(orc_t *o) { reconstruct(o); }
+/* the positivity option (not in the paper): depth floor as a fraction of the */
+/* cell's average depth, 0 = off (the default)                                */
+void orc_set_positivity(orc_t *o, double floor_fraction) { o->pos_floor = floor_fraction; }
 void orc_eval(const orc_t *o, int c, double x, double y, double *val6, double *grad12) {
   double p[2] = {x, y}, v[NVAR], g[NVAR][2];
   eval_cell(o, c, p, v, g);

@@ -58,6 +58,7 @@ def lib():
         _lib.orc_mass.argtypes = [p, p]
         _lib.orc_cell_geometry.argtypes = [p, p, p, p]
         _lib.orc_reconstruct.argtypes = [p]
+        _lib.orc_set_positivity.argtypes = [p, d]
         _lib.orc_eval.argtypes = [p, i, d, d, p, p]
         _lib.orc_omega.argtypes = [p, p]
         _lib.orc_weight_departure.argtypes = [p, p]
@@ -173,6 +174,13 @@ class Oracle:
         out = np.zeros(self.nt * 6)
         lib().orc_weight_departure(self._h, _ptr(out))
         return out.reshape(self.nt, 6)
+
+    def set_positivity(self, floor_fraction):
+        """The positivity option (not in the paper; 0 = off, the default):
+        point depths held to floor_fraction of the cell's average depth by
+        scaling the layer's depth and discharge polynomials, point velocities
+        held within the edge's two cells' average velocities."""
+        lib().orc_set_positivity(self._h, float(floor_fraction))
 
     def set_linear_mask(self, mask):
         """Cells with mask = 1 take the linear weights from now on (None: none)."""
