@@ -93,7 +93,20 @@ typedef struct {
  *   second; n > 0 polls at most n - 1 times, so 1 gives up at once. A block
  *   that gives up records GKS2L_ETIMEOUT, waits once more (up to one second)
  *   so that no copy outlives it, and writes nothing; a test sets 1 to raise
- *   the code without a fault. */
+ *   the code without a fault.
+ * positivity_floor: an option that is not in the paper (0, the default, is
+ *   the method as the paper states it). With a fraction f in (0, 1): after
+ *   each reconstruction, a layer whose depth at one of the cell's six edge
+ *   Gauss points falls below f times its cell-average depth has its depth
+ *   and discharge polynomials scaled toward their averages by one factor so
+ *   that the least point depth is f times the average (averages unchanged),
+ *   and in a layer whose point depths dip below half its average the edge
+ *   solution's side velocities are bounded by the two cells' average
+ *   velocities. It carries the paper's large-jump cases (Riemann problem II,
+ *   the circular interface), on which the method as read reaches a vacuum at
+ *   an interface state in its first steps. Runs with it take the plain
+ *   reconstruction, interface and edge kernels at their default launch
+ *   shapes (the gate, where on, still decides the linear cells). */
 typedef struct {
   double g, chi, cfl;
   double eps, eps_num;
@@ -102,6 +115,7 @@ typedef struct {
   int32_t indicator;
   float indicator_threshold;
   int32_t staging_poll_limit;
+  double positivity_floor;
 } gks2l_params;
 
 /* Run statistics (FP64 sums taken on the device). */

@@ -120,7 +120,47 @@ template <typename R> struct ReconOcc { static constexpr int value = 8; };
 template <> struct ReconOcc<double> { static constexpr int value = 4; };
 template <typename R> constexpr unsigned recon_smem() { return TileLayout<R>::BAR + 16; }
 
+// Positivity option (not in the paper), on a tile's staged side records: for
+// each cell and layer the least depth at the cell's six edge Gauss points;
+// below pos_floor times the cell-average depth, the layer's depth and
+// discharge polynomials are scaled toward their averages by one factor so
+// that it meets the floor (the lower layer's level keeps the bottom's linear
+// part); a layer whose point depths dip below half its average is flagged
+// for the edge solution's velocity bound. One thread per (cell, layer).
 template <typename R>
+__device__ void recon_positivity(const Dev &d, const Par &p, int j, int lay, R *rec) {
+  const int N = d.cs, NE = d.ne;
+  const R *xl = (const R *)d.exiL, *xr = (const R *)d.exiR;
+  R hmin = (R)INFINITY;
+  for (int f = 0; f < 3; f++) {
+    const int ce = d.cedge[f * N + j], e = ce >= 0 ? ce : ~ce;
+    const R *xs = ce >= 0 ? xl : xr;
+    for (int q = 0; q < 2; q++) {
+      const R x = xs[(2 * q) * NE + e], y = xs[(2 * q + 1) * NE + e];
+      R v[3];
+      rec_values<R>(rec, x, y, v);
+      const R h = ref_depth<R>(d, lay, e, q) + v[0];
+      hmin = h < hmin ? h : hmin;
+    }
+  }
+  const R hbar = lay == 0 ? ((const R *)d.hrefc)[j] + rec[10] : ((const R *)d.refR)[2 * d.inst[j]] + rec[10];
+  ((R *)d.pos_hbar)[lay * N + j] = hbar;
+  d.pos_flag[lay * N + j] = hmin < (R)0.5 * hbar ? 1 : 0;
+  const R fl = (R)p.pos_floor * hbar;
+  if (!(hmin < fl)) return;
+  R th = (hbar - fl) / (hbar - hmin);
+  th = th > (R)0 ? th : (R)0;
+  for (int i = 0; i < 3; i++)
+    for (int k = 0; k < 10; k++) rec[12 * i + k] *= th;
+  if (lay == 0) {
+    // eta1 = h1 + B: the bottom's linear part (slope x cell scale) stays
+    const R ih = rec[11];
+    rec[1] += ((R)1 - th) * rec[23] / ih;
+    rec[2] += ((R)1 - th) * rec[35] / ih;
+  }
+}
+
+template <typename R, bool POS = false>
 __global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p) {
   using T = TileLayout<R>;
   extern __shared__ __align__(128) unsigned char sm[];
@@ -208,6 +248,12 @@ __global__ void __launch_bounds__(192, ReconOcc<R>::value) k_recon(Dev d, Par p)
     r1[23] = r1[35] = 0;
   }
   __syncthreads();
+  if (POS) {
+    if (threadIdx.y < 2 && j < d.nt && active) {
+      recon_positivity<R>(d, p, j, threadIdx.y, stg + ((size_t)threadIdx.y * TW + threadIdx.x) * NREC);
+    }
+    __syncthreads();
+  }
   // coalesced write-out: each layer's records of the tile are contiguous, and
   // so is the staging tile, so the copy moves 16-byte vectors
   constexpr int V = 16 / sizeof(R);                 // values per vector
@@ -450,7 +496,7 @@ __device__ __forceinline__ void iface_body(const Dev &d) {
   ((R *)d.hc)[ell * d.ne + e] = iface_unit<R>(d, e, ell);
 }
 
-template <typename R>
+template <typename R, bool POS = false>
 __device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   int e = tid >> 2, ell = (tid >> 1) & 1, q = tid & 1;
@@ -459,7 +505,7 @@ __device__ __forceinline__ void edge_body(const Dev &d, const Par &p, int stage)
   // its instance's dt is known, so the unit's loads issue at once; only
   // edges of instances still running are written
   R out[12], own[2];
-  edge_unit<R, false, true>(d, p, ee, ell, q, stage, out, nullptr, own);
+  edge_unit<R, false, true, POS>(d, p, ee, ell, q, stage, out, nullptr, own);
   const bool ok = e < d.ne && d.dt[d.inst[d.eL[ee]]] > 0;
   own_write<R>(d, e, ell, q, own, ok);
   // the Gauss point q = 0 thread averages the fluxes (out[0..5]), the q = 1
@@ -628,6 +674,9 @@ template <typename R, int BS>
 __global__ void __launch_bounds__(BS, 768 / BS) k_edgef(Dev d, Par p, int stage) { edge_fused_body<R>(d, p, stage); }
 template <typename R, int BS>
 __global__ void __launch_bounds__(BS) k_update(Dev d, Par p, int stage) { update_body<R>(d, p, stage); }
+// the edge solution with the positivity option (one launch shape)
+template <typename R>
+__global__ void __launch_bounds__(128) k_edge_pos(Dev d, Par p, int stage) { edge_body<R, true>(d, p, stage); }
 template <typename R>
 __global__ void __launch_bounds__(128, 8) k_iface_r64(Dev d) { iface_body<R>(d); }
 template <typename R>
@@ -907,6 +956,8 @@ size_t layout(gks2l_ctx *c, char *base) {
   d.mlp = k.take<MlpDev>(1);
   d.gate_mask = k.take<unsigned>(cs / TW);
   d.gate_next = k.take<unsigned>(cs / TW);
+  d.pos_flag = k.take<unsigned char>(2 * cs);
+  d.pos_hbar = k.take<char>(rs * 2 * cs);
   d.wdev = k.take<float>(6 * cs);
   d.eL = k.take<int>(ne);
   d.eR = k.take<int>(ne);
@@ -1046,6 +1097,7 @@ Par make_par(const gks2l_ctx *c) {
   p.logit_out = nullptr;
   p.all_active = 0;
   p.staging_polls = c->par.staging_poll_limit;
+  p.pos_floor = c->par.positivity_floor;
   return p;
 }
 
@@ -1076,7 +1128,8 @@ void launch_gate(gks2l_ctx *c, const Par &p, cudaStream_t st) {
 template <typename R>
 void launch_recon(gks2l_ctx *c, const Par &p) {
   const Dev &d = c->d;
-  k_recon<R><<<blocks(d.nt, TW), dim3(TW, 6), recon_smem<R>(), c->stream>>>(d, p);
+  if (p.pos_floor > 0) k_recon<R, true><<<blocks(d.nt, TW), dim3(TW, 6), recon_smem<R>(), c->stream>>>(d, p);
+  else k_recon<R><<<blocks(d.nt, TW), dim3(TW, 6), recon_smem<R>(), c->stream>>>(d, p);
 }
 
 // launch shapes the autotuner chooses from: 0: 64 threads, 1: 128 threads,
@@ -1102,6 +1155,10 @@ void launch_iface(gks2l_ctx *c, cudaStream_t st) {
 template <typename R>
 void launch_edge(gks2l_ctx *c, const Par &p, int stage, cudaStream_t st) {
   const size_t n = 4 * (size_t)c->d.ne;
+  if (p.pos_floor > 0) {
+    k_edge_pos<R><<<blocks(n, 128), 128, 0, st>>>(c->d, p, stage);
+    return;
+  }
   GKS2L_SHAPE_SWITCH(c->shape[1], k_edge, n, st, c->d, p, stage)
 }
 
@@ -1127,7 +1184,9 @@ void launch_update(gks2l_ctx *c, const Par &p, int stage, cudaStream_t st) {
 // fused pass plus the deferred edges (gate variants 0-7), or as the plain
 // interface and edge kernels (8-15), which a gate that calls few cells
 // smooth leaves faster.
-inline bool fused_edges(const gks2l_ctx *c, const Par &p) { return p.use_gate && !gate_plain_edges(c->shape[3]); }
+inline bool fused_edges(const gks2l_ctx *c, const Par &p) {
+  return p.use_gate && !gate_plain_edges(c->shape[3]) && !(p.pos_floor > 0);
+}
 
 // the gate on the second stream, from this point of the main stream on
 template <typename R>
@@ -1264,7 +1323,8 @@ int create_impl(int n, const gks2l_mesh *meshes, const gks2l_params *params, gks
   else gks2l_default_params(&c->par);
   if (!(c->par.g > 0) || !(c->par.cfl > 0) || !(c->par.eps > 0) || c->par.eps_num < 0 || !(c->par.chi > 0) ||
       !(c->par.weno_gamma_hi > 0 && c->par.weno_gamma_hi <= 1) || c->par.weno_eps < 0 ||
-      (c->par.precision != GKS2L_FP64 && c->par.precision != GKS2L_FP32) || c->par.staging_poll_limit < 0) {
+      (c->par.precision != GKS2L_FP64 && c->par.precision != GKS2L_FP32) || c->par.staging_poll_limit < 0 ||
+      !(c->par.positivity_floor >= 0 && c->par.positivity_floor < 1)) {
     delete c;
     return GKS2L_EINVAL;
   }
@@ -1296,6 +1356,7 @@ int gks2l_default_params(gks2l_params *p) {
   p->indicator = GKS2L_INDICATOR_OFF;
   p->indicator_threshold = 0.5f;
   p->staging_poll_limit = 0;
+  p->positivity_floor = 0;
   return GKS2L_OK;
 }
 
@@ -1388,6 +1449,9 @@ int gks2l_bind(gks2l_ctx *c, void *d_workspace, size_t bytes, void *stream) {
   }
   CK(cudaFuncSetAttribute(k_recon<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, recon_smem<float>()));
   CK(cudaFuncSetAttribute(k_recon<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, recon_smem<double>()));
+  CK(cudaFuncSetAttribute(k_recon<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, recon_smem<float>()));
+  CK(cudaFuncSetAttribute(k_recon<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          recon_smem<double>()));
   c->bound = true;
   c->has_state = false;
   return upload_bathymetry(c);

@@ -78,6 +78,11 @@ struct Dev {
   const void *mlp;          // gate network, packed image (MlpDev)
   unsigned *gate_mask;      // per tile of 32 cells: bit i = cell i takes the linear weights
   unsigned *gate_next;      // the gate's mask for the next reconstruction (k_update copies it over)
+  // positivity option (not in the paper): per layer (0 lower, 1 upper) and
+  // cell, whether the edge states' velocities are bounded, and the cell's
+  // average depth
+  unsigned char *pos_flag;  // [2][cs]
+  void *pos_hbar;           // [2][cs], type R
                             // (written by one reconstruction for the next)
   float *wdev;              // [6][cell] max_k |omega_k / gamma_k - 1| (harvesting)
   // per edge
@@ -115,6 +120,7 @@ struct Par {
   int all_active;                            // reconstruct every instance (harvesting)
   int harvest;                               // record the weights' departure from linear
   int staging_polls;                         // > 0: operator staging polls at most this many - 1 times
+  double pos_floor;                          // positivity option (not in the paper): 0 = off
 };
 
 // a parameter in the form's precision
@@ -861,7 +867,10 @@ __host__ __device__ __forceinline__ void plane_grad(const Dev &d, int c, int whi
 // PAIRED (the edge kernels' thread layout, where the lane two over holds the
 // same point and side for the other layer): the other layer's level
 // gradient comes from that lane by a shuffle instead of from its record.
-template <typename R, bool FUSED = false, bool PAIRED = false>
+// POS (the positivity option, not in the paper): on a side whose cell's
+// layer has point depths below half its average, the side velocity is
+// bounded by the edge's two cells' average velocities of the layer.
+template <typename R, bool FUSED = false, bool PAIRED = false, bool POS = false>
 __host__ __device__ inline bool edge_unit(const Dev &d, const Par &p, int e, int ell, int q, int stage, R out[12],
                                           R *blend = nullptr, R *own = nullptr) {
   const int NE = d.ne;
@@ -925,6 +934,28 @@ __host__ __device__ inline bool edge_unit(const Dev &d, const Par &p, int e, int
       outv[k][0] = dhh;
       outv[k][1] = dmx * n0 + dmy * n1;
       outv[k][2] = -dmx * n1 + dmy * n0;
+    }
+  }
+  if (POS) {
+    const int N = d.cs, vm = ell == 0 ? 4 : 1;
+    const bool bl = d.pos_flag[ell * N + cL] != 0, br = d.pos_flag[ell * N + cR] != 0;
+    if (bl || br) {
+      const R *hb = (const R *)d.pos_hbar;
+      R un[2], ut[2];
+      for (int sd = 0; sd < 2; sd++) {
+        const int c = sd == 0 ? cL : cR, x = sd == 0 ? 0 : xf;
+        const R mx = img_dq<R>(d, vm, c, x), my = img_dq<R>(d, vm + 1, c, x);
+        const R ih = (R)1 / hb[ell * N + c];
+        un[sd] = (mx * n0 + my * n1) * ih;
+        ut[sd] = (-mx * n1 + my * n0) * ih;
+      }
+      const R ulo = un[0] < un[1] ? un[0] : un[1], uhi = un[0] < un[1] ? un[1] : un[0];
+      const R tlo = ut[0] < ut[1] ? ut[0] : ut[1], thi = ut[0] < ut[1] ? ut[1] : ut[0];
+      for (int sd = 0; sd < 2; sd++) {
+        if (!(sd == 0 ? bl : br)) continue;
+        U[sd] = U[sd] < ulo ? ulo : (U[sd] > uhi ? uhi : U[sd]);
+        V[sd] = V[sd] < tlo ? tlo : (V[sd] > thi ? thi : V[sd]);
+      }
     }
   }
   // each side's own level at the point: the interlayer source's values (R16)

@@ -54,7 +54,7 @@ class gks2l_params(ctypes.Structure):
     _fields_ = [("g", _D), ("chi", _D), ("cfl", _D), ("eps", _D), ("eps_num", _D),
                 ("weno_gamma_hi", _D), ("weno_eps", _D), ("precision", ctypes.c_int32),
                 ("indicator", ctypes.c_int32), ("indicator_threshold", ctypes.c_float),
-                ("staging_poll_limit", ctypes.c_int32)]
+                ("staging_poll_limit", ctypes.c_int32), ("positivity_floor", _D)]
 
 
 class gks2l_stats_t(ctypes.Structure):
