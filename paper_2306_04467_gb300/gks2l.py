@@ -248,6 +248,8 @@ class Solver:
                 if x.dtype != np.float64 or not x.flags.c_contiguous or (writable and not x.flags.writeable):
                     raise ValueError("host arrays must be C-contiguous float64" + (" and writable" if writable else ""))
                 return x.ctypes.data
+            if x.is_cuda or x.dtype != self.torch.float64 or not x.is_contiguous():
+                raise ValueError("tensors must be contiguous float64 CPU tensors (pinned for overlap)")
             return x.data_ptr()
 
         arr = ctypes.c_void_p * max(n, 1)

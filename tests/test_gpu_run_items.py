@@ -90,3 +90,6 @@ def test_run_items_rejects_bad_arguments():
         s.run_items([(np.ascontiguousarray(prob.avg), None)], [(np.zeros((6, nt)), None)], -1)
     assert e.value.code == g.GKS2L_EINVAL
     s.run_items([], [], 2)   # nothing to do
+    on_gpu = torch.zeros(6 * nt, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        s.run_items([(on_gpu, None)], [(np.zeros((6, nt)), None)], 2)
