@@ -1393,6 +1393,8 @@ void orc_reconstruct(orc_t *o) { reconstruct(o); }
 /* the positivity option (not in the paper): depth floor as a fraction of the */
 /* cell's average depth, 0 = off (the default)                                */
 void orc_set_positivity(orc_t *o, double floor_fraction) { o->pos_floor = floor_fraction; }
+/* the option's scaling alone, on the current reconstruction (pins) */
+void orc_positivity_scale(orc_t *o) { if (o->pos_floor > 0) positivity_scale(o); }
 void orc_eval(const orc_t *o, int c, double x, double y, double *val6, double *grad12) {
   double p[2] = {x, y}, v[NVAR], g[NVAR][2];
   eval_cell(o, c, p, v, g);

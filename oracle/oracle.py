@@ -59,6 +59,7 @@ def lib():
         _lib.orc_cell_geometry.argtypes = [p, p, p, p]
         _lib.orc_reconstruct.argtypes = [p]
         _lib.orc_set_positivity.argtypes = [p, d]
+        _lib.orc_positivity_scale.argtypes = [p]
         _lib.orc_eval.argtypes = [p, i, d, d, p, p]
         _lib.orc_omega.argtypes = [p, p]
         _lib.orc_weight_departure.argtypes = [p, p]
@@ -181,6 +182,12 @@ class Oracle:
         scaling the layer's depth and discharge polynomials, point velocities
         held within the edge's two cells' average velocities."""
         lib().orc_set_positivity(self._h, float(floor_fraction))
+
+    def positivity_scale(self):
+        """Apply the option's polynomial scaling to the current
+        reconstruction (after reconstruct(); the velocity bound is not
+        involved)."""
+        lib().orc_positivity_scale(self._h)
 
     def set_linear_mask(self, mask):
         """Cells with mask = 1 take the linear weights from now on (None: none)."""

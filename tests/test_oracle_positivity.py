@@ -52,3 +52,50 @@ def test_riemann_problem_two_runs_with_the_option():
         assert 0.15 <= a[v].min() and a[v].max() <= 1.85, (v, a[v].min(), a[v].max())
     surface = a[0] + a[3]
     assert np.abs(surface - 2.0).max() <= 0.05, np.abs(surface - 2.0).max()
+
+
+def point_depths(o, prob, b):
+    """Least depth per cell and layer (0: lower h1, 1: upper h2) over the
+    cell's edge Gauss points, from the current reconstruction; b(x) is the
+    bottom (linear, so its vertex interpolation is exact)."""
+    xq, lr = o.edge_points()
+    hmin = np.full((prob.mesh.n_tri, 2), np.inf)
+    for e in range(xq.shape[0]):
+        for q in range(2):
+            x, y = xq[e, q]
+            for c in lr[e]:
+                if c < 0:
+                    continue
+                v, _ = o.eval(c, x, y)
+                hmin[c, 0] = min(hmin[c, 0], v[3] - b(x))
+                hmin[c, 1] = min(hmin[c, 1], v[0])
+    return hmin
+
+
+def test_scaling_brings_the_least_point_depth_to_the_floor():
+    """The scaling step alone on Riemann problem II's jump over a sloping
+    bottom (b = 0.03 x, so the lower layer's level keeps the bottom's linear
+    part), after one stage of the method as read (whose reconstruction then
+    overshoots to point depths of -0.4 times the average): a layer whose
+    least point depth was below f times its average ends with that least
+    depth exactly at f times the average; every other layer keeps its
+    reconstruction, bit for bit."""
+    base = inputs.riemann_two(8)
+    b = lambda x: 0.03 * x
+    bv = b(base.mesh.xy[:, 0])
+    prob = inputs.Problem("riemann_two_slope", base.mesh, bv, base.avg, base.grad, g=base.g, chi=base.chi,
+                          cfl=base.cfl, t_end=base.t_end)
+    f = 0.3
+    o = Oracle.from_problem(prob)
+    o.advance(1)
+    o.reconstruct()
+    before = point_depths(o, prob, b)
+    o.set_positivity(f)
+    o.positivity_scale()
+    after = point_depths(o, prob, b)
+    a, _ = o.get_state()
+    hbar = np.stack([a[3], a[0]], 1)
+    scaled = before < f * hbar
+    assert scaled.any() and not scaled.all()
+    assert np.allclose(after[scaled], f * hbar[scaled], rtol=0, atol=1e-12)
+    assert np.array_equal(after[~scaled], before[~scaled])
